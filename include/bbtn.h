@@ -1,0 +1,230 @@
+/*
+ * bbtn.h -- C ABI of the GB300 (sm_103a) Branch-and-Bound Tensor Network library.
+ *
+ * Method: Wang, Gao, Zhang, Pan, Liu, "Branch-and-Bound Tensor Networks for Exact
+ * Ground-State Characterization", arXiv:2602.05470.
+ *
+ * The library contracts tropical tensor networks over the counting max-plus
+ * semiring. Every tensor element is an int32 value plus an exact degeneracy count
+ * carried as residues modulo up to BBTN_MAX_PRIMES primes p_t = 2^61 - c_t.
+ *
+ * Conventions shared by every call
+ *  - Return value: BBTN_OK (0) or a negative BBTN_E* code; bbtn_last_error() gives
+ *    a message for the calling thread's most recent failure.
+ *  - Semiring (paper Eq. (2) and the counting paragraph after it, in max-plus
+ *    form): (a, c) (+) (b, d) = (max(a,b), c + d if a == b else the count of the
+ *    larger); (a, c) (x) (b, d) = (a + b, c * d). The paper's min-sum network for an
+ *    energy H is contracted as the max-plus network of -H. "-infinity" (the hard
+ *    constraint (inf, 0) of the MWIS paragraph) is the value BBTN_NEG with count 0;
+ *    every contraction floors values at BBTN_NEG, and any value below
+ *    BBTN_FINITE_MIN is infeasible.
+ *  - Tensors are over binary variables. A tensor of rank r has 2^r elements; bit i
+ *    of the linear index is the value of variable labels[i] (labels are caller-
+ *    chosen non-negative ints). Storage is structure-of-arrays: an int32 value
+ *    plane of 2^r entries and np uint64 count planes, plane t at count + t*2^r.
+ *  - "Device pointer" arguments must point to memory of the current CUDA device;
+ *    "host" arguments to host memory. The caller owns every buffer it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Device-level calls are asynchronous on that stream unless stated otherwise.
+ */
+#ifndef BBTN_H
+#define BBTN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BBTN_OK 0
+#define BBTN_EINVAL (-1)     /* bad argument */
+#define BBTN_ENOMEM (-2)     /* out of memory, or the space cap cannot be met */
+#define BBTN_EOVERFLOW (-3)  /* degeneracy may exceed the CRT range: use more primes */
+#define BBTN_ETIMEOUT (-4)   /* a bounded device wait gave up */
+#define BBTN_EIO (-5)        /* file could not be read or parsed */
+#define BBTN_ECUDA (-6)      /* a CUDA runtime call failed */
+#define BBTN_ESTATE (-7)     /* call out of order (e.g. result before solve) */
+
+#define BBTN_NEG (-(1 << 29))           /* -infinity sentinel (value plane) */
+#define BBTN_FINITE_MIN (-(1 << 28))    /* values below this are infeasible */
+#define BBTN_MAX_PRIMES 8
+#define BBTN_MAX_RANK 30
+
+/* ------------------------------------------------------------------ library info */
+
+/* Version string of the library build. */
+const char *bbtn_version(void);
+
+/* Message of the calling thread's last failure ("" if none). Never NULL. */
+const char *bbtn_last_error(void);
+
+/* The first n primes used for count residues, written to primes[0..n-1] (host).
+ * p_t = 2^61 - c_t, c_t ascending, each proven prime by deterministic
+ * Miller-Rabin at library load. n <= BBTN_MAX_PRIMES + 1 (the last one is the
+ * check prime used by the overflow guard). */
+int bbtn_primes(int n, uint64_t *primes);
+
+/* -------------------------------------------------------- device-level operations */
+/*
+ * One counting-tropical pairwise contraction (paper Eq. (2), one binary step of
+ * contract(T)), computed entirely on the device:
+ *     C[lc] = max(BBTN_NEG, max_s A[la] + B[lb]),  s = (la U lb) \ lc,
+ *     cC_t[lc] = sum over maximising s of cA_t * cB_t  (mod p_t),  t < np.
+ * la, lb, lc: host int arrays of ra, rb, rc distinct labels; every label of lc
+ * must occur in la or lb. Labels in la or lb but not in lc are summed (labels
+ * private to one operand included). rb = 0 with lb/vb/cb NULL makes B the
+ * scalar (0, 1): a single-operand reduction.
+ * va, vb, vc: device int32 value planes; ca, cb, cc: device uint64 count planes
+ * (np planes each; unused when np == 0, the value-only mode). primes: host array of
+ * np primes of the form 2^61 - c with c < 2^10 (as returned by bbtn_primes).
+ * Input counts must already be reduced (< p_t). Output buffers must not alias
+ * inputs. Ranks up to BBTN_MAX_RANK. Asynchronous on `stream`.
+ */
+int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca,
+                  int rb, const int32_t *lb, const int32_t *vb, const uint64_t *cb,
+                  int rc, const int32_t *lc, int32_t *vc, uint64_t *cc,
+                  int np, const uint64_t *primes, void *stream);
+
+/*
+ * Bit permutation of a rank-r tensor (the layout change in front of a pairwise
+ * step): out[j] = in[i] where bit perm[q] of i equals bit q of j, i.e. output bit
+ * q is input bit perm[q]. perm: host array, a permutation of 0..r-1. Copies the
+ * value plane and np count planes (device pointers, no aliasing).
+ */
+int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,
+                 int32_t *vout, uint64_t *cout, int np, void *stream);
+
+/*
+ * Counting-(+) over n scalars (branch aggregation, paper: the final result is
+ * the sum of the contractions of each branch): v* = max_b v_b and
+ * c*_t = sum over b with v_b == v* of c_{b,t} mod p_t. vals: device int32[n];
+ * counts: device uint64[np][n] (plane t at counts + t*n); out_val: device int32[1];
+ * out_counts: device uint64[np]. n == 0 gives (BBTN_NEG, 0). Uses scratch memory
+ * from the library's stream-ordered pool. Asynchronous on `stream`.
+ */
+int bbtn_aggregate(int64_t n, const int32_t *vals, const uint64_t *counts, int np,
+                   const uint64_t *primes, int32_t *out_val, uint64_t *out_counts,
+                   void *stream);
+
+/*
+ * Tropical back-propagation through one pairwise step (the backward pass that
+ * recovers an optimal configuration): for each of `q` selected output entries
+ * sel_o[i] of C = contract(A, B) (values only), find the smallest summed
+ * assignment s (as an integer whose bit j is the j-th summed label, in the order
+ * (la \ lc) then (lb \ (la U lc))) with A + B == C[sel_o[i]], and write the
+ * matching linear indices of A and B to sel_a[i], sel_b[i]. sel_* are device
+ * int64 arrays; entries whose C value is infeasible get -1. Values only: the
+ * count planes are not read.
+ */
+int bbtn_contract_backward(int ra, const int32_t *la, const int32_t *va,
+                           int rb, const int32_t *lb, const int32_t *vb,
+                           int rc, const int32_t *lc, const int32_t *vc,
+                           int64_t q, const int64_t *sel_o, int64_t *sel_a, int64_t *sel_b,
+                           void *stream);
+
+/* ------------------------------------------------------------ solver (host-driven) */
+
+typedef struct bbtn_ctx bbtn_ctx;   /* opaque; owned by the library */
+
+#define BBTN_MODE_PLAIN 0    /* one contraction of the whole network (no slicing) */
+#define BBTN_MODE_SLICED 1   /* dynamic slicing until the space cap holds */
+#define BBTN_MODE_BBTN 2     /* branch-and-bound tensor network */
+
+typedef struct {
+    int space_cap_log2;      /* T_target of Eq. (4), in elements per tensor (default 24) */
+    int n_primes;            /* count residues, 0 (values only) .. BBTN_MAX_PRIMES (3) */
+    uint64_t seed;           /* order finder / tie-breaking seed */
+    int mode;                /* BBTN_MODE_* (default BBTN_MODE_BBTN) */
+    int sa_iters;            /* simulated-annealing sweeps of the order finder (default 20) */
+    int region_size;         /* branching-region size |R| (default 8) */
+    int batch;               /* leaves contracted per batch (default 64) */
+    int use_gnn;             /* score branches with the learned model (default 0) */
+    int count_check;         /* overflow guard: -1 auto, 0 off, 1 on (default -1) */
+    int use_symmetry;        /* spin-flip symmetry when every field is 0 (default 1) */
+    int verbose;             /* progress to stderr (default 0) */
+    int reserved[8];
+} bbtn_opts;
+
+typedef struct {
+    double t_total_s;        /* wall time of the last bbtn_solve */
+    double t_plan_s;         /* host planning (orders, branching) */
+    double t_device_s;       /* wall time spent waiting on device work */
+    double tropical_ops;     /* sum over steps of 2^{|union of labels|} multiply-adds */
+    double bytes_moved;      /* algorithmic bytes of all contraction steps */
+    double kernel_ms;        /* device time of contraction kernels (CUDA events) */
+    int64_t nodes;           /* branch-and-bound nodes expanded */
+    int64_t leaves;          /* sub-networks contracted */
+    int64_t pruned;          /* branches discarded by bounds */
+    int64_t launches;        /* kernel launches */
+    int64_t steps;           /* pairwise contraction steps executed */
+    int sc_log2;             /* largest tensor contracted (log2 elements) */
+    double tc_log2;          /* log2 of the time complexity of the plain network */
+    double sc_plain_log2;    /* space complexity of the plain network (log2) */
+    int slices_log2;         /* |V_f| of the sliced mode */
+    int reserved[8];
+} bbtn_stats;
+
+/* Fill *opts with defaults. */
+void bbtn_default_opts(bbtn_opts *opts);
+
+/* Create a solver context on the current CUDA device. opts may be NULL (defaults). */
+int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out);
+void bbtn_destroy(bbtn_ctx *ctx);
+
+/* Use `stream` for all device work of this context (default: a private stream). */
+int bbtn_set_stream(bbtn_ctx *ctx, void *stream);
+
+/*
+ * Give the context a caller-owned device workspace (for example a block allocated
+ * by PyTorch's caching allocator). Intermediates are placed in it by the static
+ * memory planner; a plan that needs more returns BBTN_ENOMEM. Without a workspace
+ * the context allocates (and keeps) its own. ptr must stay valid until the context
+ * is destroyed or another workspace is set.
+ */
+int bbtn_set_workspace(bbtn_ctx *ctx, void *ptr, size_t bytes);
+
+/*
+ * Load a +-J / Ising instance (paper Eq. (1)): H = sum_E -J_ij s_i s_j - sum_V h_i s_i.
+ * n vertices 0..n-1, m edges; edges: host int32[2m] pairs; J: host int32[m];
+ * h2: host int32[n] holding 2*h_i (NULL = no field). |J|, |h2| <= 2^16.
+ */
+int bbtn_load_spin_glass(bbtn_ctx *ctx, int n, int m, const int32_t *edges,
+                         const int32_t *J, const int32_t *h2);
+
+/*
+ * Load a maximum-weight independent set instance (paper, MWIS paragraph):
+ * weights w: host int32[n] in 1..2^16 (NULL = unit weights, plain MIS).
+ */
+int bbtn_load_mwis(bbtn_ctx *ctx, int n, int m, const int32_t *edges, const int32_t *w);
+
+/* Load an instance file (plain text: "p spin|mwis n m", "e i j [J]", "f i h2", "w i w"). */
+int bbtn_load_file(bbtn_ctx *ctx, const char *path);
+
+/*
+ * Solve the loaded instance. want_count: compute the exact degeneracy;
+ * want_config: also recover one optimal configuration (tropical backward).
+ * Blocking. Results stay valid until the next load or solve.
+ */
+int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config);
+
+/* 2*H* for a spin glass (so that half-integer fields stay integral); alpha for MWIS. */
+int bbtn_get_energy(bbtn_ctx *ctx, int64_t *e);
+
+/* Count residues: res[t] = D mod primes[t], t < *k (host arrays of >= BBTN_MAX_PRIMES). */
+int bbtn_get_count_residues(bbtn_ctx *ctx, uint64_t *res, uint64_t *primes, int *k);
+
+/* Degeneracy D as a decimal string (CRT / Garner recombination of the residues).
+ * *needed receives strlen + 1; buf may be NULL to query. */
+int bbtn_get_count_dec(bbtn_ctx *ctx, char *buf, size_t cap, size_t *needed);
+
+/* One optimal configuration: s[i] in {-1,+1} (spin glass) or {0,1} (MWIS). Host int8[n]. */
+int bbtn_get_config(bbtn_ctx *ctx, int8_t *s);
+
+/* Statistics of the last solve. */
+int bbtn_get_stats(bbtn_ctx *ctx, bbtn_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BBTN_H */

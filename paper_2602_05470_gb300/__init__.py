@@ -1,0 +1,206 @@
+"""GB300 (sm_103a) Branch-and-Bound Tensor Networks -- Python binding.
+
+Wang, Gao, Zhang, Pan, Liu, "Branch-and-Bound Tensor Networks for Exact
+Ground-State Characterization" (arXiv:2602.05470).
+
+Thin layer over the C ABI of ``libbbtn.so`` (include/bbtn.h): it marshals
+arguments and uses PyTorch only for device memory and streams. Every step of the
+contraction path runs in the library's CUDA kernels; if the library is missing
+the import of a compute function fails (there is no CPU fallback).
+
+Device-level calls (one contraction step, permute, aggregate, backward):
+    contract, permute, aggregate, contract_backward
+Solver (host-driven plain / sliced / branch-and-bound contraction):
+    Solver(opts...).solve(instance) -> Result
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+from . import _lib
+from ._lib import (BBTNError, FINITE_MIN, MAX_PRIMES, MODE_BBTN, MODE_PLAIN, MODE_SLICED, NEG,  # noqa: F401
+                   Opts, Stats, check, i32_array, u64_array)
+
+__all__ = ["primes", "contract", "permute", "aggregate", "contract_backward", "Solver", "Result",
+           "BBTNError", "NEG", "FINITE_MIN", "MODE_PLAIN", "MODE_SLICED", "MODE_BBTN", "lib_path"]
+
+
+def lib_path() -> str:
+    return _lib.LIB_PATH
+
+
+def primes(n: int = 3):
+    """The first n count primes p_t = 2^61 - c_t of the library."""
+    lib = _lib.load()
+    buf = (C.c_uint64 * max(n, 1))()
+    check(lib.bbtn_primes(n, buf))
+    return [int(buf[i]) for i in range(n)]
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def contract(la, va, ca, lb, vb, cb, lc, primes_, out=None, stream=None):
+    """One counting-tropical pairwise contraction on the device.
+
+    va/vb: int32 CUDA tensors of 2^r values; ca/cb: uint64-as-int64 CUDA tensors of
+    shape [np, 2^r] or None (unit counts). lb=None: single-operand reduction.
+    Returns (vc, cc) CUDA tensors (cc None when np == 0).
+    """
+    import torch
+    lib = _lib.load()
+    np_ = len(primes_)
+    rc = len(lc)
+    dev = va.device
+    if out is None:
+        vc = torch.empty(1 << rc, dtype=torch.int32, device=dev)
+        cc = torch.empty((np_, 1 << rc), dtype=torch.int64, device=dev) if np_ else None
+    else:
+        vc, cc = out
+    rb = 0 if lb is None else len(lb)
+    check(lib.bbtn_contract(len(la), i32_array(la), _ptr(va), _ptr(ca),
+                            rb, i32_array(lb or []), _ptr(vb), _ptr(cb),
+                            rc, i32_array(lc), _ptr(vc), _ptr(cc), np_, u64_array(primes_),
+                            _stream(stream)))
+    return vc, cc
+
+
+def permute(perm, vin, cin, stream=None):
+    """out bit q <- in bit perm[q] for the value plane and the count planes."""
+    import torch
+    lib = _lib.load()
+    r = len(perm)
+    vout = torch.empty_like(vin)
+    cout = torch.empty_like(cin) if cin is not None else None
+    np_ = 0 if cin is None else cin.shape[0]
+    check(lib.bbtn_permute(r, i32_array(perm), _ptr(vin), _ptr(cin), _ptr(vout), _ptr(cout), np_,
+                           _stream(stream)))
+    return vout, cout
+
+
+def aggregate(vals, cnts, primes_, stream=None):
+    """Counting-sum over n scalars: (max value, sum of counts at the max)."""
+    import torch
+    lib = _lib.load()
+    np_ = len(primes_)
+    ov = torch.empty(1, dtype=torch.int32, device=vals.device)
+    oc = torch.empty(max(np_, 1), dtype=torch.int64, device=vals.device)
+    check(lib.bbtn_aggregate(vals.numel(), _ptr(vals), _ptr(cnts), np_, u64_array(primes_), _ptr(ov),
+                             _ptr(oc), _stream(stream)))
+    return ov, oc[:np_]
+
+
+def contract_backward(la, va, lb, vb, lc, vc, sel_o, stream=None):
+    """Tropical arg-max of one step: linear indices of A and B attaining C[sel_o]."""
+    import torch
+    lib = _lib.load()
+    q = sel_o.numel()
+    sa = torch.empty(q, dtype=torch.int64, device=va.device)
+    sb = torch.empty(q, dtype=torch.int64, device=va.device)
+    rb = 0 if lb is None else len(lb)
+    check(lib.bbtn_contract_backward(len(la), i32_array(la), _ptr(va), rb, i32_array(lb or []), _ptr(vb),
+                                     len(lc), i32_array(lc), _ptr(vc), q, _ptr(sel_o), _ptr(sa), _ptr(sb),
+                                     _stream(stream)))
+    return sa, sb
+
+
+@dataclasses.dataclass
+class Result:
+    kind: str
+    energy2: Optional[int]        # 2 H* (spin glass)
+    alpha: Optional[int]          # MWIS optimum
+    count: Optional[int]          # exact degeneracy (CRT)
+    residues: list
+    primes: list
+    config: Optional[list]
+    stats: dict
+
+
+class Solver:
+    """Owns one library context (a CUDA stream + device arena)."""
+
+    def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
+                 sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
+                 count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 0,
+                 stream=None, workspace=None):
+        lib = _lib.load()
+        o = Opts()
+        lib.bbtn_default_opts(C.byref(o))
+        o.mode, o.space_cap_log2, o.n_primes, o.seed = mode, space_cap_log2, n_primes, seed
+        o.sa_iters, o.region_size, o.batch, o.use_gnn = sa_iters, region_size, batch, int(use_gnn)
+        o.count_check, o.use_symmetry = count_check, int(use_symmetry)
+        o.reserved[0] = max_slices_log2
+        self._ctx = C.c_void_p()
+        check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
+        if stream is not None:
+            check(lib.bbtn_set_stream(self._ctx, int(stream)))
+        self._ws = workspace
+        if workspace is not None:
+            check(lib.bbtn_set_workspace(self._ctx, workspace.data_ptr(), workspace.numel() * workspace.element_size()))
+
+    def close(self):
+        if self._ctx:
+            _lib.load().bbtn_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, inst):
+        """inst: object with kind ('spin'|'mwis'), n, edges, J, h2, w (e.g. synth.Instance)."""
+        lib = _lib.load()
+        flat = [v for e in inst.edges for v in e]
+        if inst.kind == "spin":
+            h2 = getattr(inst, "h2", None)
+            check(lib.bbtn_load_spin_glass(self._ctx, inst.n, len(inst.edges), i32_array(flat),
+                                           i32_array(inst.J), i32_array(h2) if h2 is not None else None))
+        else:
+            w = getattr(inst, "w", None)
+            check(lib.bbtn_load_mwis(self._ctx, inst.n, len(inst.edges), i32_array(flat),
+                                     i32_array(w) if w is not None else None))
+        self._kind, self._n = inst.kind, inst.n
+
+    def load_file(self, path: str, kind: str, n: int):
+        check(_lib.load().bbtn_load_file(self._ctx, path.encode()))
+        self._kind, self._n = kind, n
+
+    def solve(self, inst=None, count: bool = True, config: bool = False) -> Result:
+        lib = _lib.load()
+        if inst is not None:
+            self.load(inst)
+        check(lib.bbtn_solve(self._ctx, int(count), int(config)))
+        e = C.c_int64()
+        check(lib.bbtn_get_energy(self._ctx, C.byref(e)))
+        res, prs, k = (C.c_uint64 * 8)(), (C.c_uint64 * 8)(), C.c_int()
+        check(lib.bbtn_get_count_residues(self._ctx, res, prs, C.byref(k)))
+        cnt = None
+        if count:
+            need = C.c_size_t()
+            check(lib.bbtn_get_count_dec(self._ctx, None, 0, C.byref(need)))
+            buf = C.create_string_buffer(need.value)
+            check(lib.bbtn_get_count_dec(self._ctx, buf, need.value, C.byref(need)))
+            cnt = int(buf.value.decode())
+        cfg = None
+        if config:
+            arr = (C.c_int8 * self._n)()
+            check(lib.bbtn_get_config(self._ctx, arr))
+            cfg = [int(arr[i]) for i in range(self._n)]
+        st = Stats()
+        check(lib.bbtn_get_stats(self._ctx, C.byref(st)))
+        spin = self._kind == "spin"
+        return Result(self._kind, e.value if spin else None, None if spin else e.value, cnt,
+                      [int(res[i]) for i in range(k.value)], [int(prs[i]) for i in range(k.value)], cfg,
+                      st.as_dict())

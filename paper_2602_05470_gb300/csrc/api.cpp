@@ -1,0 +1,408 @@
+// extern "C" entry points declared in include/bbtn.h.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "../../include/bbtn.h"
+#include "common.h"
+#include "exec.h"
+#include "kernels.h"
+#include "network.h"
+#include "solver.h"
+
+using namespace bbtn;
+
+struct bbtn_ctx {
+    bbtn_opts opts;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    Problem prob;
+    bool loaded = false;
+    bool solved = false;
+    SolveOutput out;
+    bbtn_stats stats;
+    Arena arena;
+};
+
+namespace {
+
+template <class F>
+int guarded(F &&f) {
+    try {
+        f();
+        set_error("");
+        return BBTN_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host out of memory");
+        return BBTN_ENOMEM;
+    } catch (const std::exception &e) {
+        set_error(e.what());
+        return BBTN_EINVAL;
+    }
+}
+
+void check_labels(int r, const int32_t *l, const char *what) {
+    if (r < 0 || r > BBTN_MAX_RANK) fail(BBTN_EINVAL, std::string(what) + ": rank out of range");
+    if (r > 0 && !l) fail(BBTN_EINVAL, std::string(what) + ": labels missing");
+    for (int i = 0; i < r; i++) {
+        if (l[i] < 0) fail(BBTN_EINVAL, std::string(what) + ": negative label");
+        for (int j = 0; j < i; j++)
+            if (l[i] == l[j]) fail(BBTN_EINVAL, std::string(what) + ": repeated label");
+    }
+}
+
+int find(int r, const int32_t *l, int x) {
+    for (int i = 0; i < r; i++) if (l[i] == x) return i;
+    return -1;
+}
+
+void cprimes_from(int np, const uint64_t *primes, uint32_t *c) {
+    if (np < 0 || np > kMaxPlanes) fail(BBTN_EINVAL, "np out of range");
+    if (np > 0 && !primes) fail(BBTN_EINVAL, "primes missing");
+    for (int t = 0; t < np; t++) {
+        uint64_t cc = (1ull << 61) - primes[t];
+        if (primes[t] >= (1ull << 61) || cc >= 1024 || !is_prime_u64(primes[t]))
+            fail(BBTN_EINVAL, "primes must be primes 2^61 - c with c < 1024");
+        c[t] = (uint32_t)cc;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bbtn_version(void) { return "bbtn-gb300 0.1 (sm_103a)"; }
+
+const char *bbtn_last_error(void) { return get_error(); }
+
+int bbtn_primes(int n, uint64_t *primes) {
+    return guarded([&] {
+        const auto &tab = prime_table();
+        if (n < 0 || n > (int)tab.size() || (n > 0 && !primes)) fail(BBTN_EINVAL, "bad prime count");
+        for (int i = 0; i < n; i++) primes[i] = tab[i];
+    });
+}
+
+int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca, int rb,
+                  const int32_t *lb, const int32_t *vb, const uint64_t *cb, int rc, const int32_t *lc,
+                  int32_t *vc, uint64_t *cc, int np, const uint64_t *primes, void *stream) {
+    return guarded([&] {
+        check_labels(ra, la, "A");
+        check_labels(rb, lb, "B");
+        check_labels(rc, lc, "C");
+        if (!va || !vc) fail(BBTN_EINVAL, "value planes missing");
+        if (rb > 0 && !vb) fail(BBTN_EINVAL, "B values missing");
+        if (np > 0 && !cc) fail(BBTN_EINVAL, "C counts missing");
+        ContractParams P;
+        cprimes_from(np, primes, P.cprime);
+        for (int i = 0; i < 32; i++) P.oA[i] = P.oB[i] = P.sA[i] = P.sB[i] = -1;
+        for (int i = 0; i < rc; i++) {
+            int pa = find(ra, la, lc[i]), pb = find(rb, lb, lc[i]);
+            if (pa < 0 && pb < 0) fail(BBTN_EINVAL, "output label not in A or B");
+            P.oA[i] = (int8_t)pa;
+            P.oB[i] = (int8_t)pb;
+        }
+        int rs = 0;
+        for (int i = 0; i < ra; i++)
+            if (find(rc, lc, la[i]) < 0) {
+                if (rs >= 32) fail(BBTN_EINVAL, "more than 32 summed labels");
+                P.sA[rs] = (int8_t)i;
+                P.sB[rs] = (int8_t)find(rb, lb, la[i]);
+                rs++;
+            }
+        for (int i = 0; i < rb; i++)
+            if (find(rc, lc, lb[i]) < 0 && find(ra, la, lb[i]) < 0) {
+                if (rs >= 32) fail(BBTN_EINVAL, "more than 32 summed labels");
+                P.sA[rs] = -1;
+                P.sB[rs] = (int8_t)i;
+                rs++;
+            }
+        P.rc = rc;
+        P.rs = rs;
+        P.np = np;
+        P.hasB = rb > 0 || vb != nullptr;
+        P.A.val = va;
+        P.A.cnt = ca;
+        P.A.plane = 1ull << ra;
+        P.A.unit_counts = ca == nullptr;
+        if (P.hasB) {
+            P.B.val = vb;
+            P.B.cnt = cb;
+            P.B.plane = 1ull << rb;
+            P.B.unit_counts = cb == nullptr;
+        }
+        P.vc = vc;
+        P.cc = cc;
+        P.planeC = 1ull << rc;
+        cudaError_t e = launch_contract(P, (cudaStream_t)stream);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract: ") + cudaGetErrorString(e));
+    });
+}
+
+int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin, int32_t *vout,
+                 uint64_t *cout, int np, void *stream) {
+    return guarded([&] {
+        if (r < 0 || r > BBTN_MAX_RANK || np < 0 || np > kMaxPlanes) fail(BBTN_EINVAL, "bad rank / np");
+        if (!vin || !vout || (np > 0 && (!cin || !cout)) || (r > 0 && !perm)) fail(BBTN_EINVAL, "null buffer");
+        bool seen[32] = {false};
+        for (int q = 0; q < r; q++) {
+            if (perm[q] < 0 || perm[q] >= r || seen[perm[q]]) fail(BBTN_EINVAL, "perm is not a permutation");
+            seen[perm[q]] = true;
+        }
+        cudaError_t e = launch_permute(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np,
+                                       (cudaStream_t)stream);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("permute: ") + cudaGetErrorString(e));
+    });
+}
+
+int bbtn_aggregate(int64_t n, const int32_t *vals, const uint64_t *counts, int np, const uint64_t *primes,
+                   int32_t *out_val, uint64_t *out_counts, void *stream) {
+    return guarded([&] {
+        if (n < 0 || !out_val || (n > 0 && !vals) || (np > 0 && (!out_counts || (n > 0 && !counts))))
+            fail(BBTN_EINVAL, "bad aggregate arguments");
+        uint32_t c[kMaxPlanes];
+        cprimes_from(np, primes, c);
+        cudaStream_t s = (cudaStream_t)stream;
+        size_t sb = aggregate_scratch_bytes(n, np);
+        void *scratch = nullptr;
+        if (sb) BBTN_CUDA(cudaMallocAsync(&scratch, sb, s));
+        cudaError_t e = launch_aggregate(n, vals, counts, (uint64_t)n, np, c, out_val, out_counts, 1, scratch, s);
+        if (scratch) cudaFreeAsync(scratch, s);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("aggregate: ") + cudaGetErrorString(e));
+    });
+}
+
+int bbtn_contract_backward(int ra, const int32_t *la, const int32_t *va, int rb, const int32_t *lb,
+                           const int32_t *vb, int rc, const int32_t *lc, const int32_t *vc, int64_t q,
+                           const int64_t *sel_o, int64_t *sel_a, int64_t *sel_b, void *stream) {
+    return guarded([&] {
+        check_labels(ra, la, "A");
+        check_labels(rb, lb, "B");
+        check_labels(rc, lc, "C");
+        if (q < 0 || (q > 0 && (!sel_o || !sel_a || !sel_b)) || !va || !vc) fail(BBTN_EINVAL, "bad arguments");
+        BackwardParams B;
+        for (int i = 0; i < 32; i++) B.oA[i] = B.oB[i] = B.sA[i] = B.sB[i] = -1;
+        for (int i = 0; i < rc; i++) {
+            int pa = find(ra, la, lc[i]), pb = find(rb, lb, lc[i]);
+            if (pa < 0 && pb < 0) fail(BBTN_EINVAL, "output label not in A or B");
+            B.oA[i] = (int8_t)pa;
+            B.oB[i] = (int8_t)pb;
+        }
+        int rs = 0;
+        for (int i = 0; i < ra; i++)
+            if (find(rc, lc, la[i]) < 0) {
+                B.sA[rs] = (int8_t)i;
+                B.sB[rs] = (int8_t)find(rb, lb, la[i]);
+                rs++;
+            }
+        for (int i = 0; i < rb; i++)
+            if (find(rc, lc, lb[i]) < 0 && find(ra, la, lb[i]) < 0) {
+                B.sA[rs] = -1;
+                B.sB[rs] = (int8_t)i;
+                rs++;
+            }
+        if (rs > 32) fail(BBTN_EINVAL, "more than 32 summed labels");
+        B.rc = rc;
+        B.rs = rs;
+        B.hasB = rb > 0 || vb != nullptr;
+        B.va = va;
+        B.vb = vb;
+        B.vc = vc;
+        cudaError_t e = launch_backward(B, q, sel_o, sel_a, sel_b, (cudaStream_t)stream);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("backward: ") + cudaGetErrorString(e));
+    });
+}
+
+void bbtn_default_opts(bbtn_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->space_cap_log2 = 24;
+    o->n_primes = 3;
+    o->seed = 1;
+    o->mode = BBTN_MODE_BBTN;
+    o->sa_iters = 20;
+    o->region_size = 8;
+    o->batch = 64;
+    o->use_gnn = 0;
+    o->count_check = -1;
+    o->use_symmetry = 1;
+    o->verbose = 0;
+}
+
+int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
+    return guarded([&] {
+        if (!out) fail(BBTN_EINVAL, "out is NULL");
+        auto ctx = std::make_unique<bbtn_ctx>();
+        if (opts) ctx->opts = *opts;
+        else bbtn_default_opts(&ctx->opts);
+        const bbtn_opts &o = ctx->opts;
+        if (o.space_cap_log2 < 1 || o.space_cap_log2 > 30) fail(BBTN_EINVAL, "space_cap_log2 outside 1..30");
+        if (o.n_primes < 0 || o.n_primes > BBTN_MAX_PRIMES) fail(BBTN_EINVAL, "n_primes outside 0..8");
+        if (o.mode < 0 || o.mode > 2) fail(BBTN_EINVAL, "unknown mode");
+        if (o.region_size < 1 || o.region_size > 16) fail(BBTN_EINVAL, "region_size outside 1..16");
+        if (o.batch < 1) fail(BBTN_EINVAL, "batch < 1");
+        if (o.sa_iters < 0) fail(BBTN_EINVAL, "sa_iters < 0");
+        BBTN_CUDA(cudaGetDevice(&ctx->device));
+        BBTN_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+        memset(&ctx->stats, 0, sizeof(ctx->stats));
+        *out = ctx.release();
+    });
+}
+
+void bbtn_destroy(bbtn_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->arena.release();
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int bbtn_set_stream(bbtn_ctx *ctx, void *stream) {
+    return guarded([&] {
+        if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
+        if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+        ctx->stream = (cudaStream_t)stream;
+        ctx->own_stream = false;
+    });
+}
+
+int bbtn_set_workspace(bbtn_ctx *ctx, void *ptr, size_t bytes) {
+    return guarded([&] {
+        if (!ctx || (!ptr && bytes)) fail(BBTN_EINVAL, "bad workspace");
+        if (!ptr) ctx->arena.release();
+        else ctx->arena.adopt(ptr, bytes);
+    });
+}
+
+static int load_common(bbtn_ctx *ctx, Problem &&p) {
+    return guarded([&] {
+        validate(p);
+        ctx->prob = std::move(p);
+        ctx->loaded = true;
+        ctx->solved = false;
+    });
+}
+
+int bbtn_load_spin_glass(bbtn_ctx *ctx, int n, int m, const int32_t *edges, const int32_t *J,
+                         const int32_t *h2) {
+    if (!ctx || n < 1 || m < 0 || (m > 0 && (!edges || !J))) {
+        set_error("bad arguments to bbtn_load_spin_glass");
+        return BBTN_EINVAL;
+    }
+    Problem p;
+    p.kind = kSpin;
+    p.n = n;
+    for (int k = 0; k < m; k++) {
+        p.ei.push_back(edges[2 * k]);
+        p.ej.push_back(edges[2 * k + 1]);
+        p.J.push_back(J[k]);
+    }
+    p.h2.assign(n, 0);
+    if (h2) for (int i = 0; i < n; i++) p.h2[i] = h2[i];
+    return load_common(ctx, std::move(p));
+}
+
+int bbtn_load_mwis(bbtn_ctx *ctx, int n, int m, const int32_t *edges, const int32_t *w) {
+    if (!ctx || n < 1 || m < 0 || (m > 0 && !edges)) {
+        set_error("bad arguments to bbtn_load_mwis");
+        return BBTN_EINVAL;
+    }
+    Problem p;
+    p.kind = kMwis;
+    p.n = n;
+    for (int k = 0; k < m; k++) {
+        p.ei.push_back(edges[2 * k]);
+        p.ej.push_back(edges[2 * k + 1]);
+    }
+    p.w.assign(n, 1);
+    if (w) for (int i = 0; i < n; i++) p.w[i] = w[i];
+    return load_common(ctx, std::move(p));
+}
+
+int bbtn_load_file(bbtn_ctx *ctx, const char *path) {
+    return guarded([&] {
+        if (!ctx || !path) fail(BBTN_EINVAL, "bad arguments");
+        ctx->prob = read_problem_file(path);
+        ctx->loaded = true;
+        ctx->solved = false;
+    });
+}
+
+int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
+    return guarded([&] {
+        if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        ctx->solved = false;
+        BBTN_CUDA(cudaSetDevice(ctx->device));
+        Solver s(ctx->opts, ctx->stream, &ctx->arena);
+        ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
+        ctx->solved = true;
+        if (ctx->out.checked) {
+            std::vector<uint64_t> r(ctx->out.res.begin(), ctx->out.res.begin() + ctx->out.n_crt);
+            std::vector<uint64_t> p(ctx->out.primes.begin(), ctx->out.primes.begin() + ctx->out.n_crt);
+            const uint64_t q = ctx->out.primes.back();
+            if (crt_mod(r, p, q) != ctx->out.res.back())
+                fail(BBTN_EOVERFLOW, "degeneracy exceeds the range of the CRT primes; use more primes");
+        }
+    });
+}
+
+int bbtn_get_energy(bbtn_ctx *ctx, int64_t *e) {
+    return guarded([&] {
+        if (!ctx || !e) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->solved) fail(BBTN_ESTATE, "not solved");
+        // max-plus value of -2H (spin) -> 2H*; MWIS value is alpha itself
+        *e = ctx->prob.kind == kSpin ? -ctx->out.value : ctx->out.value;
+    });
+}
+
+int bbtn_get_count_residues(bbtn_ctx *ctx, uint64_t *res, uint64_t *primes, int *k) {
+    return guarded([&] {
+        if (!ctx || !k) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->solved) fail(BBTN_ESTATE, "not solved");
+        *k = ctx->out.n_crt;
+        for (int t = 0; t < ctx->out.n_crt; t++) {
+            if (res) res[t] = ctx->out.res[t];
+            if (primes) primes[t] = ctx->out.primes[t];
+        }
+    });
+}
+
+int bbtn_get_count_dec(bbtn_ctx *ctx, char *buf, size_t cap, size_t *needed) {
+    return guarded([&] {
+        if (!ctx) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->solved) fail(BBTN_ESTATE, "not solved");
+        if (ctx->out.n_crt == 0) fail(BBTN_ESTATE, "counts were not requested");
+        std::vector<uint64_t> r(ctx->out.res.begin(), ctx->out.res.begin() + ctx->out.n_crt);
+        std::vector<uint64_t> p(ctx->out.primes.begin(), ctx->out.primes.begin() + ctx->out.n_crt);
+        std::string s = crt_decimal(r, p);
+        if (needed) *needed = s.size() + 1;
+        if (buf) {
+            if (cap < s.size() + 1) fail(BBTN_EINVAL, "buffer too small");
+            memcpy(buf, s.c_str(), s.size() + 1);
+        }
+    });
+}
+
+int bbtn_get_config(bbtn_ctx *ctx, int8_t *s) {
+    return guarded([&] {
+        if (!ctx || !s) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->solved || !ctx->out.have_x) fail(BBTN_ESTATE, "no configuration (solve with want_config)");
+        for (int i = 0; i < ctx->prob.n; i++)
+            s[i] = ctx->prob.kind == kSpin ? (int8_t)(2 * ctx->out.x[i] - 1) : ctx->out.x[i];
+    });
+}
+
+int bbtn_get_stats(bbtn_ctx *ctx, bbtn_stats *st) {
+    return guarded([&] {
+        if (!ctx || !st) fail(BBTN_EINVAL, "bad arguments");
+        *st = ctx->stats;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,377 @@
+#include "exec.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+#include "common.h"
+
+namespace bbtn {
+
+namespace {
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// First-fit allocator of byte ranges inside the arena (host-side simulation; all
+// steps run in order on one stream, so a block can be reused by any step that is
+// enqueued after the last reader of its previous contents).
+struct FreeList {
+    std::map<uint64_t, uint64_t> free_;   // offset -> size
+    uint64_t top = 0, peak = 0;
+    uint64_t alloc(uint64_t bytes) {
+        bytes = align256(bytes);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                uint64_t off = it->first, sz = it->second;
+                free_.erase(it);
+                if (sz > bytes) free_[off + bytes] = sz - bytes;
+                return off;
+            }
+        }
+        // extend at the top (merge with a free block ending at top)
+        uint64_t off = top;
+        if (!free_.empty()) {
+            auto last = std::prev(free_.end());
+            if (last->first + last->second == top) {
+                off = last->first;
+                free_.erase(last);
+            }
+        }
+        top = off + bytes;
+        peak = std::max(peak, top);
+        return off;
+    }
+    void release(uint64_t off, uint64_t bytes) {
+        bytes = align256(bytes);
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+                it = pv;
+            }
+        }
+        if (it->first + it->second == top) {
+            top = it->first;
+            free_.erase(it);
+        }
+    }
+};
+
+struct View {
+    Ref ref;
+    std::vector<int> bit_label;   // label at each physical bit, -1 for a fixed bit
+    int unit = 0;
+    uint64_t block_bytes = 0;     // arena block to release (kind 1)
+    int free_rank() const {
+        int k = 0;
+        for (int l : bit_label) if (l >= 0) k++;
+        return k;
+    }
+    int pos(int label) const {
+        for (size_t i = 0; i < bit_label.size(); i++) if (bit_label[i] == label) return (int)i;
+        return -1;
+    }
+};
+
+void post_order(const CTree &t, std::vector<int> &order) {
+    order.clear();
+    std::vector<std::pair<int, int>> st{{t.root, 0}};
+    while (!st.empty()) {
+        auto &top = st.back();
+        const CNode &nd = t.nodes[top.first];
+        if (nd.is_leaf() || top.second == 2) {
+            order.push_back(top.first);
+            st.pop_back();
+            continue;
+        }
+        int child = top.second == 0 ? nd.l : nd.r;
+        top.second++;
+        st.push_back({child, 0});
+    }
+}
+
+}  // namespace
+
+uint64_t count_plane_offset_bytes(int r) { return align256(4ull << r); }
+size_t block_bytes(int r, int np) { return count_plane_offset_bytes(r) + align256((8ull << r) * np); }
+
+void DeviceNetwork::upload(const std::vector<TensorDef> &ts, int nv, cudaStream_t s) {
+    release();
+    nvars = nv;
+    offset.resize(ts.size());
+    labels.resize(ts.size());
+    std::vector<int32_t> all;
+    for (size_t i = 0; i < ts.size(); i++) {
+        offset[i] = all.size();
+        labels[i] = ts[i].labels;
+        all.insert(all.end(), ts[i].val.begin(), ts[i].val.end());
+    }
+    if (all.empty()) all.push_back(0);
+    BBTN_CUDA(cudaMalloc(&vals, all.size() * sizeof(int32_t)));
+    BBTN_CUDA(cudaMemcpyAsync(vals, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    BBTN_CUDA(cudaStreamSynchronize(s));
+}
+
+void DeviceNetwork::release() {
+    if (vals) cudaFree(vals);
+    vals = nullptr;
+}
+
+void Arena::reserve(size_t bytes) {
+    if (bytes <= size) return;
+    if (!owned) fail(BBTN_ENOMEM, "workspace too small: need " + std::to_string(bytes) + " bytes");
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+    size_t want = std::max(bytes, (size_t)1 << 20);
+    BBTN_CUDA(cudaMalloc(&ptr, want));
+    size = want;
+}
+
+void Arena::adopt(void *p, size_t bytes) {
+    release();
+    ptr = (char *)p;
+    size = bytes;
+    owned = false;
+}
+
+void Arena::release() {
+    if (ptr && owned) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+    owned = true;
+}
+
+Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
+               const uint32_t *cprime, bool keep_all) {
+    Plan plan;
+    plan.np = np;
+    plan.node_step.assign(t.nodes.size(), -1);
+    plan.node_layout.assign(t.nodes.size(), {});
+    std::vector<View> view(t.nodes.size());
+    FreeList fl;
+    std::vector<int> order;
+    post_order(t, order);
+    const uint64_t elem = 4 + 8ull * np;
+
+    auto leaf_view = [&](int id) {
+        const CNode &nd = t.nodes[id];
+        View v;
+        v.ref.kind = 0;
+        v.ref.off = net.offset[nd.leaf];
+        v.unit = 1;
+        const auto &labs = net.labels[nd.leaf];
+        for (size_t i = 0; i < labs.size(); i++) {
+            int l = labs[i];
+            if (fx[l] >= 0) {
+                v.ref.base += (uint64_t)fx[l] << i;
+                v.bit_label.push_back(-1);
+            } else {
+                v.bit_label.push_back(l);
+            }
+        }
+        return v;
+    };
+
+    auto emit = [&](int id, const View *X, const View *Y, bool is_root) {
+        // A: the operand with more free elements (reads coalesce along its low bits)
+        const View *A = X, *B = Y;
+        const CNode &nd0 = t.nodes[id];
+        int a_node = nd0.is_leaf() ? id : nd0.l, b_node = nd0.is_leaf() ? -1 : nd0.r;
+        if (B && B->free_rank() > A->free_rank()) {
+            std::swap(A, B);
+            std::swap(a_node, b_node);
+        }
+        const CNode &nd = t.nodes[id];
+        auto kept = [&](int l) { return std::binary_search(nd.lab.begin(), nd.lab.end(), l); };
+        std::vector<int> out, sum;
+        for (int l : A->bit_label) if (l >= 0) (kept(l) ? out : sum).push_back(l);
+        if (B)
+            for (int l : B->bit_label)
+                if (l >= 0 && A->pos(l) < 0) (kept(l) ? out : sum).push_back(l);
+        if (out.size() > 30) fail(BBTN_ENOMEM, "intermediate rank above 30");
+        if (sum.size() > 40) fail(BBTN_ENOMEM, "more than 40 summed labels in one step");
+        PStep st;
+        st.node = id;
+        st.a_node = a_node;
+        st.b_node = b_node;
+        ContractParams &P = st.P;
+        P.rc = (int)out.size();
+        P.rs = (int)sum.size();
+        P.hasB = B != nullptr;
+        P.np = np;
+        for (int t2 = 0; t2 < np; t2++) P.cprime[t2] = cprime[t2];
+        for (int i = 0; i < 32; i++) P.oA[i] = P.oB[i] = P.sA[i] = P.sB[i] = -1;
+        for (int i = 0; i < P.rc; i++) {
+            P.oA[i] = (int8_t)A->pos(out[i]);
+            P.oB[i] = B ? (int8_t)B->pos(out[i]) : -1;
+            st.lab_c[i] = out[i];
+        }
+        if (P.rs > 32) fail(BBTN_ENOMEM, "more than 32 summed labels in one step");
+        for (int j = 0; j < P.rs; j++) {
+            P.sA[j] = (int8_t)A->pos(sum[j]);
+            P.sB[j] = B ? (int8_t)B->pos(sum[j]) : -1;
+        }
+        st.a = A->ref;
+        P.A.unit_counts = A->unit;
+        if (B) {
+            st.b = B->ref;
+            P.B.unit_counts = B->unit;
+        }
+        View C;
+        C.bit_label = out;
+        if (is_root) {
+            C.ref.kind = 2;
+        } else {
+            C.ref.kind = 1;
+            C.block_bytes = block_bytes(P.rc, np);
+            C.ref.off = fl.alloc(C.block_bytes);
+            C.ref.plane = 1ull << P.rc;
+            C.ref.rank = P.rc;
+        }
+        st.c = C.ref;
+        st.ops = std::ldexp(1.0, P.rc + P.rs);
+        st.bytes = std::ldexp((double)(A->unit ? 4 : elem), A->free_rank()) +
+                   (B ? std::ldexp((double)(B->unit ? 4 : elem), B->free_rank()) : 0.0) +
+                   std::ldexp((double)elem, P.rc);
+        plan.ops += st.ops;
+        plan.bytes += st.bytes;
+        plan.max_rank = std::max(plan.max_rank, P.rc);
+        // operands are no longer needed once this step is enqueued
+        if (!keep_all) {
+            if (X->ref.kind == 1) fl.release(X->ref.off, X->block_bytes);
+            if (Y && Y->ref.kind == 1) fl.release(Y->ref.off, Y->block_bytes);
+        }
+        plan.node_step[id] = (int)plan.steps.size();
+        plan.node_layout[id] = out;
+        plan.steps.push_back(st);
+        return C;
+    };
+
+    for (int id : order) {
+        const CNode &nd = t.nodes[id];
+        if (nd.is_leaf()) {
+            view[id] = leaf_view(id);
+            if (id == t.root) emit(id, &view[id], nullptr, true);   // single-tensor network
+            continue;
+        }
+        view[id] = emit(id, &view[nd.l], &view[nd.r], id == t.root);
+        if (!keep_all) {
+            view[nd.l].bit_label.clear();
+            view[nd.r].bit_label.clear();
+        }
+    }
+    plan.arena_bytes = fl.peak;
+    return plan;
+}
+
+static void fill_operand(Operand &o, const Ref &r, const DeviceNetwork &net, char *arena) {
+    if (r.kind == 0) {
+        o.val = net.vals + r.off;
+        o.cnt = nullptr;
+        o.plane = 0;
+        o.base = r.base;
+    } else {
+        o.val = (const int32_t *)(arena + r.off);
+        o.cnt = (const uint64_t *)(arena + r.off + count_plane_offset_bytes(r.rank));
+        o.plane = r.plane;
+        o.base = 0;
+    }
+}
+
+void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
+              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st) {
+    for (const PStep &ps : plan.steps) {
+        ContractParams P = ps.P;
+        fill_operand(P.A, ps.a, net, arena);
+        P.A.unit_counts = ps.a.kind == 0;
+        if (P.hasB) {
+            fill_operand(P.B, ps.b, net, arena);
+            P.B.unit_counts = ps.b.kind == 0;
+        }
+        if (ps.c.kind == 2) {
+            P.vc = out_val;
+            P.cc = out_cnt;
+            P.planeC = out_plane;
+        } else {
+            P.vc = (int32_t *)(arena + ps.c.off);
+            P.cc = (uint64_t *)(arena + ps.c.off + count_plane_offset_bytes(P.rc));
+            P.planeC = 1ull << P.rc;
+        }
+        cudaError_t e = launch_contract(P, s);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract kernel: ") + cudaGetErrorString(e));
+        if (st) st->launches++;
+    }
+    if (st) {
+        st->ops += plan.ops;
+        st->bytes += plan.bytes;
+    }
+}
+
+void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net, char *arena,
+                     const int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x,
+                     cudaStream_t s) {
+    x = fx;
+    int64_t *dsel = nullptr;
+    BBTN_CUDA(cudaMalloc(&dsel, 3 * sizeof(int64_t)));
+    struct Item { int node; int64_t sel; };
+    std::vector<Item> stack{{t.root, 0}};
+    try {
+        while (!stack.empty()) {
+            Item it = stack.back();
+            stack.pop_back();
+            const int si = plan.node_step[it.node];
+            if (si < 0) fail(BBTN_ESTATE, "backward: node without a step");
+            const PStep &ps = plan.steps[si];
+            BackwardParams B;
+            ContractParams P = ps.P;
+            fill_operand(P.A, ps.a, net, arena);
+            if (P.hasB) fill_operand(P.B, ps.b, net, arena);
+            B.va = P.A.val;
+            B.vb = P.hasB ? P.B.val : nullptr;
+            B.baseA = P.A.base;
+            B.baseB = P.hasB ? P.B.base : 0;
+            B.vc = ps.c.kind == 2 ? root_val : (const int32_t *)(arena + ps.c.off);
+            B.rc = P.rc;
+            B.rs = P.rs;
+            B.hasB = P.hasB;
+            memcpy(B.oA, P.oA, 32);
+            memcpy(B.oB, P.oB, 32);
+            memcpy(B.sA, P.sA, 32);
+            memcpy(B.sB, P.sB, 32);
+            BBTN_CUDA(cudaMemcpyAsync(dsel, &it.sel, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            cudaError_t e = launch_backward(B, 1, dsel, dsel + 1, dsel + 2, s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("backward kernel: ") + cudaGetErrorString(e));
+            int64_t h[3];
+            BBTN_CUDA(cudaMemcpyAsync(h, dsel, sizeof(h), cudaMemcpyDeviceToHost, s));
+            BBTN_CUDA(cudaStreamSynchronize(s));
+            if (h[1] < 0) fail(BBTN_ESTATE, "backward: no maximising assignment (infeasible)");
+            auto handle = [&](int child, const Ref &r, int64_t idx) {
+                if (r.kind == 0) {
+                    // a network tensor: its free bits are variable values
+                    const auto &labs = net.labels[t.nodes[child].leaf];
+                    for (size_t i = 0; i < labs.size(); i++)
+                        if (fx[labs[i]] < 0) x[labs[i]] = (int8_t)((idx >> i) & 1);
+                } else {
+                    stack.push_back({child, idx});
+                }
+            };
+            handle(ps.a_node, ps.a, h[1]);
+            if (ps.P.hasB) handle(ps.b_node, ps.b, h[2]);
+        }
+    } catch (...) {
+        cudaFree(dsel);
+        throw;
+    }
+    cudaFree(dsel);
+}
+
+}  // namespace bbtn

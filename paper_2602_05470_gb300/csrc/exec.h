@@ -1,0 +1,94 @@
+// Contraction executor: turns (network, tree, fixed variables) into a list of
+// device steps with a static arena layout, runs them on a stream, and walks the
+// tree backwards to recover an optimal configuration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "kernels.h"
+#include "network.h"
+#include "order.h"
+
+namespace bbtn {
+
+// The network's original tensors, resident on the device for the whole solve.
+struct DeviceNetwork {
+    int nvars = 0;
+    int32_t *vals = nullptr;                 // all tensors' values, concatenated
+    std::vector<uint64_t> offset;            // element offset of tensor i
+    std::vector<std::vector<int>> labels;    // bit i <-> labels[i]
+    void upload(const std::vector<TensorDef> &ts, int nvars, cudaStream_t s);
+    void release();
+    ~DeviceNetwork() { release(); }
+};
+
+// Where an operand of a step lives.
+struct Ref {
+    int kind = 0;          // 0: network tensor, 1: arena block, 2: external (root destination)
+    uint64_t off = 0;      // kind 0: element offset in DeviceNetwork::vals; kind 1: byte offset
+    uint64_t plane = 0;    // count-plane stride in elements
+    uint64_t base = 0;     // constant element offset (fixed bits)
+    int rank = 0;          // kind 1: rank of the block (planes of 2^rank elements)
+};
+
+struct PStep {
+    ContractParams P;      // pointers filled at launch from the refs
+    Ref a, b, c;
+    int node = -1;
+    int a_node = -1, b_node = -1;   // tree nodes read as operand A / B
+    int lab_c[32];         // output labels (bit order of C)
+    double ops = 0;        // 2^{|union|} multiply-adds
+    double bytes = 0;      // algorithmic bytes (operands read once, result written once)
+};
+
+struct Plan {
+    std::vector<PStep> steps;
+    size_t arena_bytes = 0;
+    int np = 0;
+    double ops = 0, bytes = 0;
+    int max_rank = 0;
+    // per tree node: its step index (internal) and the bit order of its result
+    std::vector<int> node_step;
+    std::vector<std::vector<int>> node_layout;
+};
+
+// Element layout of an arena block of rank r with np count planes.
+size_t block_bytes(int r, int np);
+uint64_t count_plane_offset_bytes(int r);
+
+// Plan the contraction of the network restricted to fx (fx[v] = -1 free, else the
+// fixed value). The result (a scalar) goes to the external destination given at
+// run time. keep_all keeps every intermediate alive (for the backward walk).
+Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
+               const uint32_t *cprime, bool keep_all);
+
+struct RunStats {
+    int64_t launches = 0;
+    double ops = 0, bytes = 0;
+};
+
+// Enqueue a plan: arena = device base pointer of at least plan.arena_bytes,
+// root result to (out_val[0], out_cnt[t * out_plane]).
+void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
+              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st);
+
+// Backward walk after run_plan with keep_all: sets x[v] for every free variable
+// (fixed ones copied from fx). Synchronises the stream.
+void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net, char *arena,
+                     const int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x,
+                     cudaStream_t s);
+
+// Grow-only device arena.
+struct Arena {
+    char *ptr = nullptr;
+    size_t size = 0;
+    bool owned = true;
+    void reserve(size_t bytes);
+    void adopt(void *p, size_t bytes);       // caller-owned workspace
+    void release();
+    ~Arena() { release(); }
+};
+
+}  // namespace bbtn

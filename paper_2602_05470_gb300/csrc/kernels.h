@@ -1,0 +1,63 @@
+// Internal (C++) interface between the host planner and the sm_103a kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "semiring.cuh"
+
+namespace bbtn {
+
+// One operand of a pairwise step. Element e of the operand lives at
+// val[base + e] and cnt[t * plane + base + e]; `base` carries the constant
+// offset of variables fixed by slicing / branching (paper Eq. (3): the reduced
+// network T|_{s_Vf = x} reads a sub-block of each original tensor).
+struct Operand {
+    const int32_t *val = nullptr;
+    const uint64_t *cnt = nullptr;
+    uint64_t plane = 0;       // elements between count planes
+    uint64_t base = 0;        // constant element offset
+    int unit_counts = 0;      // 1: counts implied by values (1 if finite, else 0)
+};
+
+// C[o] = max(NEG, max_k A[offA(o) + kA(k)] + B[offB(o) + kB(k)]) with counts.
+// Output bit i of o sits at bit oA[i] of A's index (-1: not in A), likewise oB;
+// summed bit j of k sits at bit sA[j] / sB[j].
+struct ContractParams {
+    Operand A, B;
+    int32_t *vc = nullptr;
+    uint64_t *cc = nullptr;
+    uint64_t planeC = 0;
+    int rc = 0, rs = 0, hasB = 0, np = 0;
+    int8_t oA[32], oB[32], sA[32], sB[32];
+    uint32_t cprime[kMaxPlanes];
+};
+
+cudaError_t launch_contract(const ContractParams &p, cudaStream_t s);
+
+// out bit q <- in bit perm[q]
+cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,
+                           uint64_t plane_in, int32_t *vout, uint64_t *cout, uint64_t plane_out,
+                           int np, cudaStream_t s);
+
+// counting-(+) over n scalars (count plane t of the inputs at cnts + t*plane);
+// result count t at out_cnt[t * out_plane]; scratch: aggregate_scratch_bytes(n, np)
+size_t aggregate_scratch_bytes(int64_t n, int np);
+cudaError_t launch_aggregate(int64_t n, const int32_t *vals, const uint64_t *cnts, uint64_t plane,
+                             int np, const uint32_t *cprime, int32_t *out_val, uint64_t *out_cnt,
+                             uint64_t out_plane, void *scratch, cudaStream_t s);
+
+// Tropical argmax of one step for q selected outputs (values only).
+struct BackwardParams {
+    const int32_t *va = nullptr, *vb = nullptr, *vc = nullptr;
+    uint64_t baseA = 0, baseB = 0;
+    int rc = 0, rs = 0, hasB = 0;
+    int8_t oA[32], oB[32], sA[32], sB[32];
+};
+cudaError_t launch_backward(const BackwardParams &p, int64_t q, const int64_t *sel_o,
+                            int64_t *sel_a, int64_t *sel_b, cudaStream_t s);
+
+// Fill a value plane with v and np count planes with c (initialisation helper).
+cudaError_t launch_fill(int32_t *val, uint64_t *cnt, uint64_t n, uint64_t plane, int np,
+                        int32_t v, uint64_t c, cudaStream_t s);
+
+}  // namespace bbtn

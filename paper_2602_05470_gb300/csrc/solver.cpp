@@ -1,0 +1,616 @@
+#include "solver.h"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "common.h"
+
+namespace bbtn {
+
+namespace {
+
+struct Rng {
+    uint64_t s;
+    explicit Rng(uint64_t seed) : s(seed) {}
+    uint64_t next() {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (next() >> 11) * (1.0 / 9007199254740992.0); }
+    uint64_t below(uint64_t n) { return next() % n; }
+};
+
+// Largest tensor and Eq. (4) overflow of the reference tree with fixed variables
+// removed; `over` receives the overflowing nodes.
+struct Overflow {
+    int sc = 0;
+    double rho = 0;
+    std::vector<int> nodes;   // node ids with effective size > cap
+    std::vector<int> size;    // their effective sizes
+};
+
+Overflow overflow_of(const CTree &t, const std::vector<int8_t> &fx, int cap) {
+    Overflow o;
+    for (size_t i = 0; i < t.nodes.size(); i++) {
+        int s = 0;
+        for (int l : t.nodes[i].lab) if (fx[l] < 0) s++;
+        o.sc = std::max(o.sc, s);
+        if (s > cap) {
+            o.rho += s - cap;
+            o.nodes.push_back((int)i);
+            o.size.push_back(s);
+        }
+    }
+    return o;
+}
+
+}  // namespace
+
+void Solver::ensure_buffers(int64_t n) {
+    // slots 0..n-1 plus one temporary slot at index dcap_; slot 0 (the running
+    // counting-sum) survives a reallocation
+    if (n <= dcap_) return;
+    const int64_t ncap = std::max<int64_t>(n, 64);
+    const int planes = std::max(np_, 1);
+    int32_t *nv = nullptr;
+    uint64_t *nc = nullptr;
+    BBTN_CUDA(cudaMalloc(&nv, sizeof(int32_t) * (ncap + 1)));
+    BBTN_CUDA(cudaMalloc(&nc, sizeof(uint64_t) * planes * (ncap + 1)));
+    if (d_val_) {
+        BBTN_CUDA(cudaMemcpyAsync(nv, d_val_, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
+        for (int t = 0; t < np_; t++)
+            BBTN_CUDA(cudaMemcpyAsync(nc + t * (ncap + 1), d_cnt_ + t * (dcap_ + 1), sizeof(uint64_t),
+                                      cudaMemcpyDeviceToDevice, stream_));
+        BBTN_CUDA(cudaStreamSynchronize(stream_));
+    }
+    release_buffers();
+    d_val_ = nv;
+    d_cnt_ = nc;
+    dcap_ = ncap;
+    scratch_bytes_ = aggregate_scratch_bytes(dcap_ + 1, np_) + 256;
+    BBTN_CUDA(cudaMalloc(&d_scratch_, scratch_bytes_));
+}
+
+void Solver::release_buffers() {
+    if (d_val_) cudaFree(d_val_);
+    if (d_cnt_) cudaFree(d_cnt_);
+    if (d_scratch_) cudaFree(d_scratch_);
+    d_val_ = nullptr;
+    d_cnt_ = nullptr;
+    d_scratch_ = nullptr;
+    dcap_ = 0;
+}
+
+CTree Solver::order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials) {
+    std::vector<std::vector<int>> ll(net_.labels.size());
+    for (size_t i = 0; i < ll.size(); i++)
+        for (int l : net_.labels[i]) if (fx[l] < 0) ll[i].push_back(l);
+    return find_order(ll, p_->n, cap, w_rho, trials, opts_.sa_iters, opts_.seed);
+}
+
+// Exact reductions of a partial assignment (logical inference, paper: local
+// pruning eliminates provably suboptimal configurations):
+//  MWIS  - a vertex set to 1 forces its neighbours to 0;
+//        - a free vertex with no free neighbour and no neighbour set to 1 is 1
+//          (leaving it out loses w_v > 0 with nothing gained).
+//  spin  - a free spin whose neighbours are all fixed takes the sign of its
+//          effective field when that field is non-zero (the other sign is
+//          strictly worse); with zero field it stays free.
+void Solver::simplify(std::vector<int8_t> &fx) const {
+    const Problem &p = *p_;
+    bool changed = true;
+    while (changed) {
+        changed = false;
+        for (int v = 0; v < p.n; v++) {
+            if (p.kind == kMwis) {
+                if (fx[v] == 1) {
+                    for (auto &nb : p.adj[v])
+                        if (fx[nb.first] < 0) { fx[nb.first] = 0; changed = true; }
+                } else if (fx[v] < 0) {
+                    bool free_nb = false, one_nb = false;
+                    for (auto &nb : p.adj[v]) {
+                        if (fx[nb.first] < 0) free_nb = true;
+                        else if (fx[nb.first] == 1) one_nb = true;
+                    }
+                    if (one_nb) { fx[v] = 0; changed = true; }
+                    else if (!free_nb) { fx[v] = 1; changed = true; }
+                }
+            } else if (fx[v] < 0) {
+                int64_t eff = p.h2[v];
+                bool free_nb = false;
+                for (auto &nb : p.adj[v]) {
+                    if (fx[nb.first] < 0) { free_nb = true; break; }
+                    eff += 2ll * p.J[nb.second] * (2 * fx[nb.first] - 1);
+                }
+                if (!free_nb && eff != 0) { fx[v] = eff > 0 ? 1 : 0; changed = true; }
+            }
+        }
+    }
+}
+
+void Solver::setup(const Problem &p, bool want_count) {
+    p_ = &p;
+    const auto &tab = prime_table();
+    n_crt_ = want_count ? std::max(0, std::min(opts_.n_primes, BBTN_MAX_PRIMES)) : 0;
+    if (want_count && n_crt_ == 0) n_crt_ = 1;
+    check_ = false;
+    if (n_crt_ > 0) {
+        if (opts_.count_check == 1) check_ = true;
+        else if (opts_.count_check < 0) check_ = p.n + 1 > 61 * n_crt_ - 2;   // D <= 2^n
+    }
+    np_ = n_crt_ + (check_ ? 1 : 0);
+    primes_.clear();
+    for (int t = 0; t < n_crt_; t++) primes_.push_back(tab[t]);
+    if (check_) primes_.push_back(tab[kCheckPrime]);
+    for (int t = 0; t < np_; t++) cprime_[t] = (uint32_t)((1ull << 61) - primes_[t]);
+
+    fx0_.assign(p.n, -1);
+    mult_ = 1;
+    if (p.kind == kSpin && p.zero_field() && opts_.use_symmetry && p.n > 0) {
+        // H(s) = H(-s): fix the highest-degree spin to +1 and double the count
+        int best = 0;
+        for (int v = 1; v < p.n; v++) if (p.adj[v].size() > p.adj[best].size()) best = v;
+        fx0_[best] = 1;
+        mult_ = 2;
+    }
+    simplify(fx0_);
+
+    net_.upload(build_network(p), p.n, stream_);
+    const double t0 = now_s();
+    const int cap = opts_.space_cap_log2;
+    const double w_rho = opts_.mode == BBTN_MODE_PLAIN ? 8.0 : 1.0;
+    tree_ = order_for(fx0_, cap, w_rho, opts_.mode == BBTN_MODE_PLAIN ? 4 : 4);
+    Cost c = tree_cost(tree_, cap);
+    st_->tc_log2 = c.tc_log2;
+    st_->sc_plain_log2 = c.sc;
+    st_->t_plan_s += now_s() - t0;
+
+    release_buffers();
+    ensure_buffers(std::max(opts_.batch, 1) + 1);
+    cudaError_t e = launch_fill(d_val_, d_cnt_, 1, (uint64_t)dcap_ + 1, np_, kNeg, 0, stream_);
+    if (e != cudaSuccess) fail(BBTN_ECUDA, cudaGetErrorString(e));
+    best_val_ = INT64_MIN;
+    incumbent_ = INT64_MIN;
+    best_fx_.clear();
+    out_ = SolveOutput();
+}
+
+// Contract every leaf sub-network (each a full contraction of the network with its
+// fixed variables sliced out), then fold the results into the running
+// counting-sum in slot 0 (paper: the result is the sum over the branches).
+void Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves) {
+    if (leaves.empty()) return;
+    const int64_t n = (int64_t)leaves.size();
+    ensure_buffers(n + 1);   // slots 0..n, temporary at dcap_ > n
+    const uint64_t plane = (uint64_t)dcap_ + 1;
+    cudaEvent_t e0, e1;
+    BBTN_CUDA(cudaEventCreate(&e0));
+    BBTN_CUDA(cudaEventCreate(&e1));
+    BBTN_CUDA(cudaEventRecord(e0, stream_));
+    const double tw = now_s();
+    RunStats rs;
+    for (int64_t i = 0; i < n; i++) {
+        const double tp = now_s();
+        Plan plan = make_plan(tree_, net_, leaves[i], np_, cprime_, false);
+        st_->t_plan_s += now_s() - tp;
+        arena_->reserve(plan.arena_bytes);
+        st_->sc_log2 = std::max(st_->sc_log2, plan.max_rank);
+        st_->steps += (int64_t)plan.steps.size();
+        run_plan(plan, net_, arena_->ptr, d_val_ + 1 + i, d_cnt_ + 1 + i, plane, stream_, &rs);
+    }
+    // slot 0 <- counting-sum of slots 0..n
+    int32_t *tv = d_val_ + dcap_;            // temporary result slot (last entry)
+    uint64_t *tc = d_cnt_ + dcap_;
+    cudaError_t e = launch_aggregate(n + 1, d_val_, d_cnt_, plane, np_, cprime_, tv, tc, plane, d_scratch_, stream_);
+    if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("aggregate: ") + cudaGetErrorString(e));
+    rs.launches += n + 1 > 256 ? 2 : 1;
+    BBTN_CUDA(cudaMemcpyAsync(d_val_, tv, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
+    for (int t = 0; t < np_; t++)
+        BBTN_CUDA(cudaMemcpyAsync(d_cnt_ + t * plane, tc + t * plane, sizeof(uint64_t),
+                                  cudaMemcpyDeviceToDevice, stream_));
+    std::vector<int32_t> vals(n);
+    BBTN_CUDA(cudaMemcpyAsync(vals.data(), d_val_ + 1, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream_));
+    BBTN_CUDA(cudaEventRecord(e1, stream_));
+    BBTN_CUDA(cudaStreamSynchronize(stream_));
+    float ms = 0;
+    BBTN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    st_->kernel_ms += ms;
+    st_->t_device_s += now_s() - tw;
+    st_->launches += rs.launches;
+    st_->tropical_ops += rs.ops;
+    st_->bytes_moved += rs.bytes;
+    st_->leaves += n;
+    for (int64_t i = 0; i < n; i++) {
+        if (vals[i] >= kFiniteMin && vals[i] > best_val_) {
+            best_val_ = vals[i];
+            best_fx_ = leaves[i];
+        }
+        incumbent_ = std::max<int64_t>(incumbent_, vals[i] >= kFiniteMin ? vals[i] : INT64_MIN);
+    }
+}
+
+void Solver::run_plain() {
+    Overflow o = overflow_of(tree_, fx0_, opts_.space_cap_log2);
+    if (o.sc > opts_.space_cap_log2)
+        fail(BBTN_ENOMEM, "plain contraction needs 2^" + std::to_string(o.sc) +
+                              " elements, above the space cap 2^" + std::to_string(opts_.space_cap_log2));
+    contract_leaves({fx0_});
+}
+
+void Solver::run_sliced() {
+    const double t0 = now_s();
+    CTree t = tree_;
+    std::vector<int> vf = dynamic_slicing(t, opts_.space_cap_log2, std::max(1, opts_.sa_iters / 2), opts_.seed);
+    tree_ = t;
+    st_->t_plan_s += now_s() - t0;
+    st_->slices_log2 = (int)vf.size();
+    const int max_log2 = opts_.reserved[0] > 0 ? opts_.reserved[0] : 30;
+    if ((int)vf.size() > max_log2)
+        fail(BBTN_ENOMEM, "slicing needs 2^" + std::to_string(vf.size()) + " slices");
+    const uint64_t ns = 1ull << vf.size();
+    const int64_t bs = std::max(1, opts_.batch);
+    std::vector<std::vector<int8_t>> batch;
+    for (uint64_t x = 0; x < ns; x++) {
+        std::vector<int8_t> fx = fx0_;
+        for (size_t j = 0; j < vf.size(); j++) fx[vf[j]] = (int8_t)((x >> j) & 1);
+        batch.push_back(std::move(fx));
+        if ((int64_t)batch.size() == bs || x + 1 == ns) {
+            contract_leaves(batch);
+            batch.clear();
+        }
+    }
+}
+
+int64_t Solver::incumbent_heuristic() {
+    const Problem &p = *p_;
+    Rng rng(opts_.seed * 31 + 7);
+    int64_t best = INT64_MIN;
+    if (p.kind == kMwis) {
+        for (int rep = 0; rep < 8; rep++) {
+            std::vector<int8_t> x = fx0_;
+            std::vector<int> deg(p.n, 0);
+            for (int v = 0; v < p.n; v++)
+                for (auto &nb : p.adj[v]) if (x[nb.first] < 0) deg[v]++;
+            while (true) {
+                int pick = -1;
+                double bestkey = 1e300;
+                for (int v = 0; v < p.n; v++) {
+                    if (x[v] >= 0) continue;
+                    double key = (double)deg[v] / p.w[v] + (rep ? 0.5 * rng.uniform() : 0.0);
+                    if (key < bestkey) { bestkey = key; pick = v; }
+                }
+                if (pick < 0) break;
+                x[pick] = 1;
+                for (auto &nb : p.adj[pick]) {
+                    int u = nb.first;
+                    if (x[u] < 0) {
+                        x[u] = 0;
+                        for (auto &nb2 : p.adj[u]) deg[nb2.first]--;
+                    }
+                }
+            }
+            for (auto &v : x) if (v < 0) v = 0;
+            int64_t val = objective(p, x);
+            best = std::max(best, val);
+        }
+    } else {
+        for (int rep = 0; rep < 8; rep++) {
+            std::vector<int8_t> x(p.n);
+            for (int v = 0; v < p.n; v++) x[v] = fx0_[v] >= 0 ? fx0_[v] : (int8_t)(rng.next() & 1);
+            // greedy single-spin flips until no flip raises -2H
+            bool improved = true;
+            while (improved) {
+                improved = false;
+                for (int v = 0; v < p.n; v++) {
+                    if (fx0_[v] >= 0) continue;
+                    int64_t field = p.h2[v];
+                    for (auto &nb : p.adj[v]) field += 2ll * p.J[nb.second] * (2 * x[nb.first] - 1);
+                    int s = 2 * x[v] - 1;
+                    if (field * s < 0) { x[v] ^= 1; improved = true; }
+                }
+            }
+            best = std::max(best, objective(p, x));
+        }
+    }
+    return best;
+}
+
+void Solver::run_bbtn() {
+    const Problem &p = *p_;
+    const int cap = opts_.space_cap_log2;
+    const int K = std::max(2, std::min(opts_.region_size, 10));
+    incumbent_ = incumbent_heuristic();
+    struct BNode {
+        std::vector<int8_t> fx;
+        int64_t ub;
+    };
+    std::vector<BNode> stack;
+    stack.push_back({fx0_, upper_bound(p, fx0_)});
+    std::vector<std::vector<int8_t>> batch;
+    const int bs = std::max(1, opts_.batch);
+    std::vector<double> score(p.n);
+    std::vector<int> pow3(K + 1, 1);
+    for (int i = 1; i <= K; i++) pow3[i] = pow3[i - 1] * 3;
+
+    while (!stack.empty() || !batch.empty()) {
+        if (stack.empty() || (int)batch.size() >= bs) {
+            contract_leaves(batch);
+            batch.clear();
+            continue;
+        }
+        BNode nd = std::move(stack.back());
+        stack.pop_back();
+        if (nd.ub < incumbent_) { st_->pruned++; continue; }     // global pruning (ties kept)
+        st_->nodes++;
+        const double tp = now_s();
+        Overflow ov = overflow_of(tree_, nd.fx, cap);
+        if (ov.sc <= cap) {
+            batch.push_back(std::move(nd.fx));
+            st_->t_plan_s += now_s() - tp;
+            continue;
+        }
+        // ---- branching region R: seed = variable carried by the most overflow
+        std::fill(score.begin(), score.end(), 0.0);
+        for (size_t q = 0; q < ov.nodes.size(); q++)
+            for (int l : tree_.nodes[ov.nodes[q]].lab)
+                if (nd.fx[l] < 0) score[l] += ov.size[q] - cap;
+        int seed = -1;
+        for (int v = 0; v < p.n; v++)
+            if (nd.fx[v] < 0 && score[v] > 0 && (seed < 0 || score[v] > score[seed])) seed = v;
+        if (seed < 0) fail(BBTN_ESTATE, "no branching variable");
+        std::vector<int> R{seed};
+        std::vector<char> inR(p.n, 0);
+        inR[seed] = 1;
+        while ((int)R.size() < K) {
+            int pick = -1;
+            double pk = -1;
+            for (int v : R)
+                for (auto &nb : p.adj[v]) {
+                    int u = nb.first;
+                    if (inR[u] || nd.fx[u] >= 0) continue;
+                    int links = 0;
+                    for (auto &nb2 : p.adj[u]) if (inR[nb2.first]) links++;
+                    double key = score[u] + 0.25 * links;
+                    if (key > pk) { pk = key; pick = u; }
+                }
+            if (pick < 0) break;
+            R.push_back(pick);
+            inR[pick] = 1;
+        }
+        const int k = (int)R.size();
+        // ---- feasible local configurations F(R): boundary equivalence (per boundary
+        // state keep every configuration of maximal local value -- ties kept)
+        std::vector<int> bpos;    // indices into R of boundary variables
+        for (int i = 0; i < k; i++) {
+            bool b = false;
+            for (auto &nb : p.adj[R[i]]) if (!inR[nb.first] && nd.fx[nb.first] < 0) { b = true; break; }
+            if (b) bpos.push_back(i);
+        }
+        std::vector<int64_t> lval(1u << k);
+        std::vector<char> feas(1u << k, 1);
+        for (uint32_t c = 0; c < (1u << k); c++) {
+            int64_t val = 0;
+            for (int i = 0; i < k && feas[c]; i++) {
+                const int v = R[i];
+                const int xi = (c >> i) & 1;
+                if (p.kind == kMwis) {
+                    if (xi) {
+                        val += p.w[v];
+                        for (auto &nb : p.adj[v]) {
+                            int u = nb.first;
+                            if (nd.fx[u] == 1) { feas[c] = 0; break; }
+                            if (inR[u]) {
+                                int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
+                                if ((c >> j) & 1) { feas[c] = 0; break; }
+                            }
+                        }
+                    }
+                } else {
+                    int64_t eff = p.h2[v];
+                    for (auto &nb : p.adj[v]) {
+                        int u = nb.first;
+                        if (nd.fx[u] >= 0) eff += 2ll * p.J[nb.second] * (2 * nd.fx[u] - 1);
+                        else if (inR[u] && u > v) {
+                            int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
+                            val += 2ll * p.J[nb.second] * (2 * xi - 1) * (2 * ((c >> j) & 1) - 1);
+                        }
+                    }
+                    val += eff * (2 * xi - 1);
+                }
+            }
+            lval[c] = val;
+        }
+        const int nb = (int)bpos.size();
+        std::vector<int64_t> bestb(1u << nb, INT64_MIN);
+        auto bstate = [&](uint32_t c) {
+            uint32_t b = 0;
+            for (int q = 0; q < nb; q++) b |= ((c >> bpos[q]) & 1u) << q;
+            return b;
+        };
+        for (uint32_t c = 0; c < (1u << k); c++)
+            if (feas[c]) bestb[bstate(c)] = std::max(bestb[bstate(c)], lval[c]);
+        if (p.kind == kMwis) {
+            // fewer boundary members never constrain the outside more: a strictly
+            // better configuration on a subset of the boundary dominates
+            for (int q = 0; q < nb; q++)
+                for (uint32_t b = 0; b < (1u << nb); b++)
+                    if ((b >> q) & 1) bestb[b] = std::max(bestb[b], bestb[b ^ (1u << q)]);
+        }
+        std::vector<uint32_t> F;
+        for (uint32_t c = 0; c < (1u << k); c++)
+            if (feas[c] && lval[c] == bestb[bstate(c)]) F.push_back(c);
+        if (F.empty()) { st_->pruned++; st_->t_plan_s += now_s() - tp; continue; }
+        // ---- optimal branching D(R): a decision tree over R whose leaves (clauses)
+        // are complete and orthogonal by construction; minimise gamma of
+        // gamma^rho = sum_i gamma^rho_i (Eq. (4) and the characteristic equation)
+        std::vector<uint64_t> nmask(ov.nodes.size(), 0);   // R-bits carried by each overflow node
+        std::vector<int> idxR(p.n, -1);
+        for (int i = 0; i < k; i++) idxR[R[i]] = i;
+        // MWIS: a 1 in R also fixes its free neighbours (outside R too): universe U
+        std::vector<int> U(R.begin(), R.end());
+        std::vector<int> idxU(p.n, -1);
+        for (int i = 0; i < k; i++) idxU[R[i]] = i;
+        std::vector<uint64_t> nbmask(k, 0);
+        if (p.kind == kMwis) {
+            for (int i = 0; i < k; i++)
+                for (auto &nbp : p.adj[R[i]]) {
+                    int u = nbp.first;
+                    if (nd.fx[u] >= 0) continue;
+                    if (idxU[u] < 0 && (int)U.size() < 64) { idxU[u] = (int)U.size(); U.push_back(u); }
+                    if (idxU[u] >= 0) nbmask[i] |= 1ull << idxU[u];
+                }
+        }
+        for (size_t q = 0; q < ov.nodes.size(); q++)
+            for (int l : tree_.nodes[ov.nodes[q]].lab)
+                if (idxU[l] >= 0 && nd.fx[l] < 0) nmask[q] |= 1ull << idxU[l];
+        const int S = pow3[k];
+        std::vector<double> rho(S);
+        std::vector<char> cons(S);
+        for (int s = 0; s < S; s++) {
+            uint64_t fixedm = 0;
+            uint32_t m = 0, vv = 0;
+            int x = s;
+            for (int i = 0; i < k; i++, x /= 3) {
+                int d = x % 3;
+                if (d) {
+                    fixedm |= 1ull << i;
+                    m |= 1u << i;
+                    if (d == 2) { vv |= 1u << i; fixedm |= nbmask[i]; }
+                }
+            }
+            double r = 0;
+            for (size_t q = 0; q < ov.nodes.size(); q++) {
+                int sz = ov.size[q] - __builtin_popcountll(nmask[q] & fixedm);
+                if (sz > cap) r += sz - cap;
+            }
+            rho[s] = r;
+            char any = 0;
+            for (uint32_t c : F) if ((c & m) == vv) { any = 1; break; }
+            cons[s] = any;
+        }
+        const double rho0 = rho[0];
+        std::vector<double> memo(S);
+        std::vector<int> choice(S);
+        std::vector<int> by_fixed(S);      // states, most fixed variables first
+        {
+            std::vector<int> nfix(S);
+            for (int s = 0; s < S; s++) {
+                int x = s, nf = 0;
+                for (int i = 0; i < k; i++, x /= 3) if (x % 3) nf++;
+                nfix[s] = nf;
+                by_fixed[s] = s;
+            }
+            std::stable_sort(by_fixed.begin(), by_fixed.end(), [&](int a, int b) { return nfix[a] > nfix[b]; });
+        }
+        auto dp = [&](double gamma) {
+            for (int s : by_fixed) {
+                if (!cons[s]) { memo[s] = 0; choice[s] = -1; continue; }
+                double best = s == 0 ? INFINITY : std::pow(gamma, rho[s] - rho0);
+                int bc = -1;
+                int x = s;
+                for (int i = 0; i < k; i++, x /= 3) {
+                    if (x % 3) continue;
+                    double c = memo[s + pow3[i]] + memo[s + 2 * pow3[i]];
+                    if (c < best) { best = c; bc = i; }
+                }
+                memo[s] = best;
+                choice[s] = bc;
+            }
+            return memo[0];
+        };
+        double lo = 1.0, hi = std::ldexp(1.0, k) + 1;
+        for (int it = 0; it < 40; it++) {
+            double mid = std::sqrt(lo * hi);
+            if (dp(mid) <= 1.0) hi = mid; else lo = mid;
+        }
+        dp(hi);
+        std::vector<int> clause_states;
+        std::function<void(int)> collect = [&](int s) {
+            if (!cons[s]) return;
+            if (choice[s] < 0) { clause_states.push_back(s); return; }
+            collect(s + pow3[choice[s]]);
+            collect(s + 2 * pow3[choice[s]]);
+        };
+        collect(0);
+        st_->t_plan_s += now_s() - tp;
+        // ---- children: fix each clause, propagate, bound
+        std::vector<BNode> kids;
+        for (int s : clause_states) {
+            BNode ch;
+            ch.fx = nd.fx;
+            int x = s;
+            for (int i = 0; i < k; i++, x /= 3)
+                if (x % 3) ch.fx[R[i]] = (int8_t)(x % 3 - 1);
+            simplify(ch.fx);
+            ch.ub = upper_bound(p, ch.fx);
+            if (ch.ub < incumbent_) { st_->pruned++; continue; }
+            kids.push_back(std::move(ch));
+        }
+        std::sort(kids.begin(), kids.end(), [](const BNode &a, const BNode &b) { return a.ub < b.ub; });
+        for (auto &ch : kids) stack.push_back(std::move(ch));   // best bound popped first
+    }
+}
+
+void Solver::finish(bool want_config) {
+    const uint64_t plane = (uint64_t)dcap_ + 1;
+    int32_t v = 0;
+    std::vector<uint64_t> r(np_);
+    BBTN_CUDA(cudaMemcpyAsync(&v, d_val_, sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
+    for (int t = 0; t < np_; t++)
+        BBTN_CUDA(cudaMemcpyAsync(&r[t], d_cnt_ + t * plane, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream_));
+    BBTN_CUDA(cudaStreamSynchronize(stream_));
+    if (v < kFiniteMin) fail(BBTN_ESTATE, "no feasible configuration");
+    out_.value = v;
+    for (int t = 0; t < np_; t++) r[t] = mulmod_host(r[t], mult_ % primes_[t], primes_[t]);
+    out_.res = r;
+    out_.primes = primes_;
+    out_.n_crt = n_crt_;
+    out_.checked = check_;
+    if (want_config) {
+        if (best_fx_.empty() || best_val_ != v) fail(BBTN_ESTATE, "optimal branch not recorded");
+        Plan plan = make_plan(tree_, net_, best_fx_, 0, cprime_, true);
+        arena_->reserve(plan.arena_bytes);
+        int32_t *root = d_val_ + dcap_;
+        RunStats rs;
+        run_plan(plan, net_, arena_->ptr, root, nullptr, 0, stream_, &rs);
+        backward_config(plan, tree_, net_, arena_->ptr, root, best_fx_, out_.x, stream_);
+        st_->launches += rs.launches + (int64_t)plan.steps.size();
+        for (auto &xv : out_.x) if (xv < 0) xv = 0;   // variables absent from every tensor
+        if (objective(*p_, out_.x) != out_.value)
+            fail(BBTN_ESTATE, "recovered configuration does not attain the optimum");
+        out_.have_x = true;
+    }
+}
+
+SolveOutput Solver::solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st) {
+    const double t0 = now_s();
+    st_ = st;
+    memset(st, 0, sizeof(*st));
+    try {
+        setup(p, want_count);
+        switch (opts_.mode) {
+            case BBTN_MODE_PLAIN: run_plain(); break;
+            case BBTN_MODE_SLICED: run_sliced(); break;
+            default: run_bbtn(); break;
+        }
+        finish(want_config);
+    } catch (...) {
+        release_buffers();
+        net_.release();
+        throw;
+    }
+    release_buffers();
+    net_.release();
+    st->t_total_s = now_s() - t0;
+    return out_;
+}
+
+}  // namespace bbtn

@@ -1,0 +1,72 @@
+// Host-driven solver: plain contraction, dynamic slicing and the branch-and-bound
+// tensor network driver (paper: TN with Slicing and Branch-and-Bound Tensor
+// Network sections).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bbtn.h"
+#include "exec.h"
+#include "network.h"
+#include "order.h"
+
+namespace bbtn {
+
+struct SolveOutput {
+    int64_t value = 0;                 // max-plus value of the network (-2H* or alpha)
+    std::vector<uint64_t> res;         // residues (CRT primes first, check prime last if used)
+    std::vector<uint64_t> primes;
+    int n_crt = 0;                     // residues that enter the CRT
+    bool checked = false;              // last residue is the overflow check
+    std::vector<int8_t> x;             // optimal configuration (0/1 per variable)
+    bool have_x = false;
+};
+
+class Solver {
+  public:
+    Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena) : opts_(o), stream_(s), arena_(arena) {}
+    SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
+
+  private:
+    struct Leafset;
+    void setup(const Problem &p, bool want_count);
+    void contract_leaves(const std::vector<std::vector<int8_t>> &leaves);
+    void finish(bool want_config);
+    void run_plain();
+    void run_sliced();
+    void run_bbtn();
+    int64_t incumbent_heuristic();
+    void simplify(std::vector<int8_t> &fx) const;
+    CTree order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
+
+    bbtn_opts opts_;
+    cudaStream_t stream_;
+    Arena *arena_;
+    const Problem *p_ = nullptr;
+    DeviceNetwork net_;
+    CTree tree_;                        // reference tree (labels of the free network)
+    std::vector<int8_t> fx0_;           // root fixed variables (symmetry)
+    int np_ = 0, n_crt_ = 0;
+    bool check_ = false;
+    std::vector<uint64_t> primes_;
+    uint32_t cprime_[kMaxPlanes] = {0};
+    uint64_t mult_ = 1;                 // count multiplier from symmetry
+    // device accumulator of branch results: slot 0 = running counting-sum
+    int32_t *d_val_ = nullptr;
+    uint64_t *d_cnt_ = nullptr;
+    int64_t dcap_ = 0;
+    void *d_scratch_ = nullptr;
+    size_t scratch_bytes_ = 0;
+    // best leaf (for the configuration)
+    int64_t best_val_ = INT64_MIN;
+    std::vector<int8_t> best_fx_;
+    int64_t incumbent_ = INT64_MIN;
+    bbtn_stats *st_ = nullptr;
+    SolveOutput out_;
+    void ensure_buffers(int64_t n);
+    void release_buffers();
+};
+
+}  // namespace bbtn

@@ -1,0 +1,200 @@
+"""Kernel-level parity: every device call through the C ABI against the CPU oracle,
+element by element, on seeded inputs (bit-exact: all arithmetic is integer)."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_05470_gb300 as P
+    return P
+
+
+def _rand(rng, r, np_, lo=-3, hi=3, neg_frac=0.0, unit=False):
+    v = rng.integers(lo, hi + 1, size=1 << r).astype(np.int32)
+    if neg_frac:
+        v[rng.random(1 << r) < neg_frac] = oracle.NEG
+    if unit:
+        c = np.where(v >= -(1 << 28), 1, 0).astype(np.uint64)[None, :].repeat(np_, 0)
+    else:
+        c = rng.integers(0, 2**61 - 1024, size=(np_, 1 << r), dtype=np.uint64)
+        c[:, v < -(1 << 28)] = 0
+    return v, c
+
+
+def _dev(v, c):
+    dv = torch.from_numpy(v).cuda()
+    dc = torch.from_numpy(c.view(np.int64)).cuda() if c is not None and c.size else None
+    return dv, dc
+
+
+def _run(P, la, A, lb, B, lc, primes, unitA=False, unitB=False):
+    va, ca = _dev(*A)
+    if unitA:
+        ca = None
+    if lb is None:
+        vb = cb = None
+    else:
+        vb, cb = _dev(*B)
+        if unitB:
+            cb = None
+    vc, cc = P.contract(la, va, ca, lb, vb, cb, lc, primes)
+    torch.cuda.synchronize()
+    out_c = cc.cpu().numpy().view(np.uint64) if cc is not None else np.zeros((0, 1 << len(lc)), np.uint64)
+    return vc.cpu().numpy(), out_c
+
+
+CASES = [
+    # (la, lb, lc) -- covers batch/m/n/k roles, private labels, outer products,
+    # permuted outputs, scalars, and several thread blocks
+    ([0, 1, 2, 3], [2, 3, 4, 5], [0, 1, 4, 5]),                      # plain matmul-like
+    ([0, 1, 2, 3, 4, 5], [4, 5, 6, 7], [0, 1, 2, 3, 6, 7]),
+    ([0, 1, 2], [1, 2, 3], [3, 0]),                                  # permuted output
+    ([5, 1, 7, 3], [3, 7, 9], [9, 5, 1]),                            # scattered labels
+    ([0, 1, 2, 3], [2, 3, 4], [0, 1, 2, 3, 4]),                      # batch labels, no sum
+    ([0, 1, 2, 3], [4, 5], [0, 1, 2, 3, 4, 5]),                      # outer product
+    ([0, 1, 2, 3], [3, 4], [0, 4]),                                  # private labels 1, 2
+    ([0, 1], [0, 1], []),                                            # full contraction to a scalar
+    (list(range(12)), [10, 11, 12, 13], list(range(10)) + [12, 13]), # 4096 outputs x 4
+    (list(range(3, 16)), [0, 1, 2, 3], list(range(0, 3)) + list(range(4, 16))),  # 2^15 outputs, low bits from B
+    (list(range(14)), [12, 13, 14], [14] + list(range(12))),         # big output, permuted top bit
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("np_", [0, 1, 3])
+def test_contract_parity(P, case, np_):
+    la, lb, lc = CASES[case]
+    rng = np.random.default_rng(100 + case)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), neg_frac=0.1)
+    B = _rand(rng, len(lb), max(np_, 1), neg_frac=0.1)
+    A = (A[0], A[1][:np_])
+    B = (B[0], B[1][:np_])
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov)
+    assert np.array_equal(cc, oc)
+
+
+@pytest.mark.parametrize("np_", [2, 8, 9])
+def test_contract_many_planes(P, np_):
+    la, lb, lc = [0, 1, 2, 3, 4], [3, 4, 5, 6], [0, 1, 2, 5, 6]
+    rng = np.random.default_rng(7)
+    primes = P.primes(np_)
+    A = _rand(rng, 5, np_, -1, 1)
+    B = _rand(rng, 4, np_, -1, 1)
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
+def test_contract_unit_counts(P):
+    """Counts omitted (NULL): implied 1 for finite entries, 0 for -infinity."""
+    la, lb, lc = [0, 1, 2, 3], [2, 3, 4], [0, 1, 4]
+    rng = np.random.default_rng(8)
+    primes = P.primes(3)
+    A = _rand(rng, 4, 3, -2, 2, neg_frac=0.2, unit=True)
+    B = _rand(rng, 3, 3, -2, 2, neg_frac=0.2, unit=True)
+    vc, cc = _run(P, la, A, lb, B, lc, primes, unitA=True, unitB=True)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
+@pytest.mark.parametrize("rs", [12, 13, 14])
+def test_contract_large_summed_extent(P, rs):
+    """More summed labels than the shared-memory table covers (2^12)."""
+    la = list(range(rs + 2))
+    lb = list(range(2, rs + 3))
+    lc = [0, 1, rs + 2]
+    rng = np.random.default_rng(rs)
+    primes = P.primes(2)
+    A = _rand(rng, len(la), 2, -2, 2)
+    B = _rand(rng, len(lb), 2, -2, 2)
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
+@pytest.mark.parametrize("la,lc", [([0, 1, 2, 3, 4], [1, 3]), ([0, 1, 2], []), (list(range(16)), list(range(4, 16)))])
+def test_reduce_parity(P, la, lc):
+    rng = np.random.default_rng(len(la))
+    primes = P.primes(3)
+    A = _rand(rng, len(la), 3, -2, 2, neg_frac=0.05)
+    vc, cc = _run(P, la, A, None, None, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], None, None, None, lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
+@pytest.mark.parametrize("r,seed", [(1, 0), (4, 1), (7, 2), (11, 3), (16, 4), (20, 5)])
+def test_permute_parity(P, r, seed):
+    rng = np.random.default_rng(seed)
+    perm = [int(x) for x in rng.permutation(r)]
+    primes = P.primes(3)
+    v, c = _rand(rng, r, 3, -5, 5)
+    dv, dc = _dev(v, c)
+    ov_, oc_ = P.permute(perm, dv, dc)
+    torch.cuda.synchronize()
+    # the permutation is the single-operand contraction with relabelled output bits
+    la = list(range(r))
+    lc = [perm[q] for q in range(r)]
+    ev, ec = oracle.contract(la, v, c, None, None, None, lc, primes)
+    assert np.array_equal(ov_.cpu().numpy(), ev)
+    assert np.array_equal(oc_.cpu().numpy().view(np.uint64), ec)
+
+
+@pytest.mark.parametrize("n", [0, 1, 7, 256, 257, 1000, 70000])
+def test_aggregate_parity(P, n):
+    rng = np.random.default_rng(n)
+    primes = P.primes(3)
+    v = rng.integers(-3, 1, size=n).astype(np.int32)
+    c = rng.integers(0, 2**61 - 1024, size=(3, n), dtype=np.uint64)
+    dv = torch.from_numpy(v).cuda()
+    dc = torch.from_numpy(c.view(np.int64).copy()).cuda()
+    ov_, oc_ = P.aggregate(dv, dc, primes)
+    torch.cuda.synchronize()
+    # oracle: pad to a power of two with (-inf, 0) and reduce every label
+    r = max(0, int(np.ceil(np.log2(max(n, 1)))))
+    pv = np.full(1 << r, oracle.NEG, np.int32)
+    pc = np.zeros((3, 1 << r), np.uint64)
+    pv[:n] = v
+    pc[:, :n] = c
+    ev, ec = oracle.contract(list(range(r)), pv, pc, None, None, None, [], primes)
+    assert int(ov_.cpu()[0]) == int(ev[0])
+    assert np.array_equal(oc_.cpu().numpy().view(np.uint64), ec[:, 0])
+
+
+def test_backward_selects_a_maximiser(P):
+    la, lb, lc = [0, 1, 2, 3, 4], [3, 4, 5, 6], [0, 1, 5, 6]
+    rng = np.random.default_rng(11)
+    va = rng.integers(-3, 3, size=32).astype(np.int32)
+    vb = rng.integers(-3, 3, size=16).astype(np.int32)
+    primes = P.primes(1)
+    ov, _ = oracle.contract(la, va, np.ones((1, 32), np.uint64), lb, vb, np.ones((1, 16), np.uint64), lc, primes)
+    dva, dvb, dvc = torch.from_numpy(va).cuda(), torch.from_numpy(vb).cuda(), torch.from_numpy(ov).cuda()
+    sel = torch.arange(16, dtype=torch.int64, device="cuda")
+    sa, sb = P.contract_backward(la, dva, lb, dvb, lc, dvc, sel)
+    sa, sb = sa.cpu().numpy(), sb.cpu().numpy()
+    for o in range(16):
+        ia, ib = int(sa[o]), int(sb[o])
+        assert va[ia] + vb[ib] == ov[o]
+        # the output labels agree with o
+        bits = {lc[i]: (o >> i) & 1 for i in range(len(lc))}
+        for i, l in enumerate(la):
+            if l in bits:
+                assert (ia >> i) & 1 == bits[l]
+        for i, l in enumerate(lb):
+            if l in bits:
+                assert (ib >> i) & 1 == bits[l]
+        # shared summed labels agree between A and B
+        for i, l in enumerate(la):
+            if l in lb and l not in bits:
+                assert (ia >> i) & 1 == (ib >> lb.index(l)) & 1

@@ -1,0 +1,148 @@
+"""End-to-end parity of the solver (plain, sliced and branch-and-bound modes)
+against the CPU oracle: ground energy / MIS size and the exact degeneracy must
+match bit for bit; returned configurations must attain the optimum."""
+import json
+import os
+
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_answers.json")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_05470_gb300 as P
+    return P
+
+
+def _energy(inst, cfg):
+    e = sum(-2 * J * cfg[i] * cfg[j] for (i, j), J in zip(inst.edges, inst.J))
+    return e + sum(-h * s for h, s in zip(inst.h2, cfg))
+
+
+def _check(inst, res, ref_opt, ref_count):
+    if inst.kind == "spin":
+        assert res.energy2 == ref_opt
+    else:
+        assert res.alpha == ref_opt
+    assert res.count == ref_count
+    for r, p in zip(res.residues, res.primes):
+        assert r == ref_count % p
+    if res.config is not None:
+        if inst.kind == "spin":
+            assert _energy(inst, res.config) == ref_opt
+        else:
+            x = res.config
+            assert all(not (x[i] and x[j]) for i, j in inst.edges)
+            assert sum(w for w, xi in zip(inst.w, x) if xi) == ref_opt
+
+
+def test_c1_spin_8x8_plain(P):
+    """8x8 +-J lattice, no field: plain counting contraction (no branching)."""
+    inst = synth.square_lattice(8, seed=synth.config_seed(1, 0))
+    e2, d = oracle.solve(inst)
+    with open(GOLDEN) as f:
+        g = json.load(f)["spin_8x8_f1"][0]
+    assert (e2, d) == (g["e2"], int(g["count"]))
+    s = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=24)
+    res = s.solve(inst, count=True, config=True)
+    _check(inst, res, e2, d)
+    assert res.count % 2 == 0
+
+
+@pytest.mark.parametrize("mode", ["plain", "sliced", "bbtn"])
+@pytest.mark.parametrize("L,h2,seed", [(4, 0, 1), (5, 1, 2), (6, 0, 3), (7, 2, 4), (10, 0, 5), (12, 0, 6)])
+def test_spin_lattice_modes(P, mode, L, h2, seed):
+    inst = synth.square_lattice(L, seed=seed, h2=h2)
+    e2, d = oracle.solve(inst)
+    m = {"plain": P.MODE_PLAIN, "sliced": P.MODE_SLICED, "bbtn": P.MODE_BBTN}[mode]
+    cap = 24 if mode == "plain" else max(3, L - 3)
+    s = P.Solver(mode=m, space_cap_log2=cap, batch=16)
+    res = s.solve(inst, count=True, config=True)
+    _check(inst, res, e2, d)
+    if mode != "plain":
+        assert res.stats["sc_log2"] <= cap
+
+
+@pytest.mark.parametrize("mode", ["plain", "sliced", "bbtn"])
+@pytest.mark.parametrize("N,weights,seed", [(5, "unit", 1), (8, "unit", 2), (10, "uniform10", 3), (12, "unit", 4),
+                                            (14, "uniform10", 5)])
+def test_ksg_modes(P, mode, N, weights, seed):
+    inst = synth.kings_subgraph(N, 0.8, seed=seed, weights=weights)
+    a, d = oracle.solve(inst)
+    m = {"plain": P.MODE_PLAIN, "sliced": P.MODE_SLICED, "bbtn": P.MODE_BBTN}[mode]
+    cap = 24 if mode == "plain" else max(3, N - 2)
+    s = P.Solver(mode=m, space_cap_log2=cap, batch=16)
+    res = s.solve(inst, count=True, config=True)
+    _check(inst, res, a, d)
+
+
+@pytest.mark.parametrize("L", [3, 6, 9])
+def test_ferromagnet_closed_form(P, L):
+    inst = synth.square_lattice(L, dist="ferro")
+    res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=max(2, L - 2)).solve(inst, count=True, config=True)
+    assert (res.energy2, res.count) == (-2 * inst.m, 2)
+
+
+def test_unique_ground_state_config_matches_oracle(P):
+    """Wide integer couplings and a field: the ground state is unique, so the
+    recovered configuration must equal the oracle's."""
+    inst = synth.square_lattice(6, seed=9, dist="uniform", jmax=1000, h2=1)
+    e2, d, cfg = oracle.spin_square_tm(inst, want_config=True)
+    assert d == 1
+    res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=4).solve(inst, count=True, config=True)
+    assert res.energy2 == e2 and res.count == 1
+    assert res.config == [int(x) for x in cfg]
+
+
+def test_prime_sets_agree(P):
+    inst = synth.square_lattice(10, seed=77)
+    a = P.Solver(mode=P.MODE_PLAIN, n_primes=3).solve(inst)
+    b = P.Solver(mode=P.MODE_PLAIN, n_primes=5).solve(inst)
+    assert a.count == b.count and a.energy2 == b.energy2
+
+
+def test_count_overflow_guard(P):
+    """70 free spins: D = 2^70 exceeds one 61-bit prime; the guard must refuse."""
+    inst = synth.empty_graph(70, kind="spin")
+    s = P.Solver(mode=P.MODE_PLAIN, n_primes=1, use_symmetry=False)
+    with pytest.raises(P.BBTNError) as ei:
+        s.solve(inst)
+    assert ei.value.code == -3
+    res = P.Solver(mode=P.MODE_PLAIN, n_primes=2, use_symmetry=False).solve(inst)
+    assert res.count == 2**70
+
+
+@pytest.mark.parametrize("kind", ["spin", "mwis"])
+def test_degenerate_graphs(P, kind):
+    for inst in (synth.empty_graph(1, kind=kind), synth.empty_graph(5, kind=kind),
+                 synth.path_graph(9, kind=kind), synth.complete_graph(6, kind=kind),
+                 synth.star_graph(7, kind=kind), synth.cycle_graph(7, kind=kind)):
+        if kind == "spin":
+            e2, d, _ = oracle.spin_bruteforce(inst)
+        else:
+            e2, d, _ = oracle.mwis_bruteforce(inst)
+        for m in (P.MODE_PLAIN, P.MODE_BBTN):
+            cap = 24 if m == P.MODE_PLAIN else 2
+            res = P.Solver(mode=m, space_cap_log2=cap).solve(inst, count=True, config=True)
+            _check(inst, res, e2, d)
+
+
+def test_ksg_30x30_bbtn_sample(P):
+    """Two instances of the 30x30 King's-subgraph workload (filling 0.8,
+    cap 2^24) against the stored oracle answers."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"]
+    for row in rows[:2]:
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+        res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24).solve(inst, count=True, config=True)
+        _check(inst, res, row["alpha"], int(row["count"]))
