@@ -143,7 +143,9 @@ typedef struct {
     int count_check;         /* overflow guard: -1 auto, 0 off, 1 on (default -1) */
     int use_symmetry;        /* spin-flip symmetry when every field is 0 (default 1) */
     int verbose;             /* progress to stderr (default 0) */
-    int reserved[8];
+    int profile;             /* time every contraction launch with CUDA events (default 0) */
+    int max_slices_log2;     /* sliced mode: refuse more than 2^this slices (default 30) */
+    int reserved[6];
 } bbtn_opts;
 
 typedef struct {
@@ -162,6 +164,14 @@ typedef struct {
     double tc_log2;          /* log2 of the time complexity of the plain network */
     double sc_plain_log2;    /* space complexity of the plain network (log2) */
     int slices_log2;         /* |V_f| of the sliced mode */
+    /* per-launch CUDA-event timing of the contraction kernels (profile mode only) */
+    double prof_ms;          /* summed device time of all contraction launches */
+    double prof_bytes;       /* their algorithmic bytes */
+    double prof_ops;         /* their multiply-adds */
+    int64_t prof_launches;
+    double prof_big_ms;      /* the same for launches moving >= 64 MiB */
+    double prof_big_bytes;
+    int64_t prof_big_launches;
     int reserved[8];
 } bbtn_stats;
 
@@ -223,6 +233,27 @@ int bbtn_get_config(bbtn_ctx *ctx, int8_t *s);
 
 /* Statistics of the last solve. */
 int bbtn_get_stats(bbtn_ctx *ctx, bbtn_stats *st);
+
+/* Host-side planning summary (no device work; usable without a GPU). */
+typedef struct {
+    double tc_log2;          /* log2 time complexity of the (unsliced) network's tree */
+    int sc_log2;             /* its space complexity (largest tensor, log2 elements) */
+    double rho;              /* Eq. (4) overflow of that tree at the space cap */
+    int slices_log2;         /* |V_f| chosen by dynamic slicing (sliced mode, else 0) */
+    int64_t steps;           /* pairwise steps of one leaf / slice */
+    double ops;              /* its multiply-adds */
+    double bytes;            /* its algorithmic bytes */
+    double arena_bytes;      /* device arena the static memory plan needs */
+    int reserved[8];
+} bbtn_plan_info;
+
+/*
+ * Plan the loaded instance on the host only: contraction order (and the slicing
+ * set in sliced mode), and the step list of the first slice (all sliced variables
+ * 0). If dump_path is not NULL, one CSV line per step is written there:
+ * rank_a, rank_b, rank_c, summed, low_identity_bits, bytes, ops.
+ */
+int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path);
 
 #ifdef __cplusplus
 }

@@ -131,15 +131,15 @@ class Solver:
 
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
-                 count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 0,
-                 stream=None, workspace=None):
+                 count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
+                 profile: bool = False, stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
         o.mode, o.space_cap_log2, o.n_primes, o.seed = mode, space_cap_log2, n_primes, seed
         o.sa_iters, o.region_size, o.batch, o.use_gnn = sa_iters, region_size, batch, int(use_gnn)
         o.count_check, o.use_symmetry = count_check, int(use_symmetry)
-        o.reserved[0] = max_slices_log2
+        o.max_slices_log2, o.profile = max_slices_log2, int(profile)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:
@@ -176,6 +176,14 @@ class Solver:
     def load_file(self, path: str, kind: str, n: int):
         check(_lib.load().bbtn_load_file(self._ctx, path.encode()))
         self._kind, self._n = kind, n
+
+    def analyze(self, inst=None, dump_path: Optional[str] = None) -> dict:
+        """Host-only planning summary (order, slicing, step list); needs no GPU."""
+        if inst is not None:
+            self.load(inst)
+        info = _lib.PlanInfo()
+        check(_lib.load().bbtn_analyze(self._ctx, C.byref(info), dump_path.encode() if dump_path else None))
+        return info.as_dict()
 
     def solve(self, inst=None, count: bool = True, config: bool = False) -> Result:
         lib = _lib.load()

@@ -29,7 +29,8 @@ class Opts(C.Structure):
     _fields_ = [("space_cap_log2", C.c_int), ("n_primes", C.c_int), ("seed", C.c_uint64),
                 ("mode", C.c_int), ("sa_iters", C.c_int), ("region_size", C.c_int),
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
-                ("use_symmetry", C.c_int), ("verbose", C.c_int), ("reserved", C.c_int * 8)]
+                ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
+                ("max_slices_log2", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class Stats(C.Structure):
@@ -38,10 +39,21 @@ class Stats(C.Structure):
                 ("nodes", C.c_int64), ("leaves", C.c_int64), ("pruned", C.c_int64),
                 ("launches", C.c_int64), ("steps", C.c_int64), ("sc_log2", C.c_int),
                 ("tc_log2", C.c_double), ("sc_plain_log2", C.c_double), ("slices_log2", C.c_int),
-                ("reserved", C.c_int * 8)]
+                ("prof_ms", C.c_double), ("prof_bytes", C.c_double), ("prof_ops", C.c_double),
+                ("prof_launches", C.c_int64), ("prof_big_ms", C.c_double), ("prof_big_bytes", C.c_double),
+                ("prof_big_launches", C.c_int64), ("reserved", C.c_int * 8)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("tc_log2", C.c_double), ("sc_log2", C.c_int), ("rho", C.c_double),
+                ("slices_log2", C.c_int), ("steps", C.c_int64), ("ops", C.c_double), ("bytes", C.c_double),
+                ("arena_bytes", C.c_double), ("reserved", C.c_int * 8)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 _lib = None
@@ -74,6 +86,7 @@ _SIGS = {
     "bbtn_get_count_dec": ([_vp, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_get_config": ([_vp, _i8p], C.c_int),
     "bbtn_get_stats": ([_vp, _P(Stats)], C.c_int),
+    "bbtn_analyze": ([_vp, _P(PlanInfo), C.c_char_p], C.c_int),
 }
 
 

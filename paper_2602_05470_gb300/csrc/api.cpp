@@ -231,6 +231,8 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->count_check = -1;
     o->use_symmetry = 1;
     o->verbose = 0;
+    o->profile = 0;
+    o->max_slices_log2 = 30;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -246,9 +248,16 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
         if (o.region_size < 1 || o.region_size > 16) fail(BBTN_EINVAL, "region_size outside 1..16");
         if (o.batch < 1) fail(BBTN_EINVAL, "batch < 1");
         if (o.sa_iters < 0) fail(BBTN_EINVAL, "sa_iters < 0");
-        BBTN_CUDA(cudaGetDevice(&ctx->device));
-        BBTN_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
-        ctx->own_stream = true;
+        // without a usable device the context still plans on the host (bbtn_analyze);
+        // every call that needs the device then fails with BBTN_ECUDA
+        if (cudaGetDevice(&ctx->device) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) == cudaSuccess) {
+            ctx->own_stream = true;
+        } else {
+            cudaGetLastError();
+            ctx->device = -1;
+            ctx->stream = nullptr;
+        }
         memset(&ctx->stats, 0, sizeof(ctx->stats));
         *out = ctx.release();
     });
@@ -338,6 +347,7 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
         if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
         ctx->solved = false;
+        if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
         BBTN_CUDA(cudaSetDevice(ctx->device));
         Solver s(ctx->opts, ctx->stream, &ctx->arena);
         ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
@@ -395,6 +405,15 @@ int bbtn_get_config(bbtn_ctx *ctx, int8_t *s) {
         if (!ctx->solved || !ctx->out.have_x) fail(BBTN_ESTATE, "no configuration (solve with want_config)");
         for (int i = 0; i < ctx->prob.n; i++)
             s[i] = ctx->prob.kind == kSpin ? (int8_t)(2 * ctx->out.x[i] - 1) : ctx->out.x[i];
+    });
+}
+
+int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path) {
+    return guarded([&] {
+        if (!ctx || !info) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        Solver s(ctx->opts, ctx->stream, &ctx->arena);
+        s.analyze(ctx->prob, info, dump_path);
     });
 }
 

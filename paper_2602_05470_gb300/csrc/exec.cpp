@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 
 #include "common.h"
@@ -103,20 +105,60 @@ void post_order(const CTree &t, std::vector<int> &order) {
 uint64_t count_plane_offset_bytes(int r) { return align256(4ull << r); }
 size_t block_bytes(int r, int np) { return count_plane_offset_bytes(r) + align256((8ull << r) * np); }
 
-void DeviceNetwork::upload(const std::vector<TensorDef> &ts, int nv, cudaStream_t s) {
+cudaEvent_t Profiler::get() {
+    if (used == pool.size()) {
+        cudaEvent_t e;
+        BBTN_CUDA(cudaEventCreate(&e));
+        pool.push_back(e);
+    }
+    return pool[used++];
+}
+
+void Profiler::collect() {
+    constexpr double kBig = 64.0 * 1024 * 1024;
+    for (const Rec &r : recs) {
+        float t = 0;
+        BBTN_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        if (dump) fprintf(dump, "%d,%d,%d,%d,%d,%.0f,%.0f,%.5f\n", r.ra, r.rb, r.rc, r.rs, r.ident, r.bytes, r.ops, t);
+        bytes += r.bytes;
+        ops += r.ops;
+        launches++;
+        if (r.bytes >= kBig) {
+            big_ms += t;
+            big_bytes += r.bytes;
+            big_launches++;
+        }
+    }
+    recs.clear();
+    used = 0;
+}
+
+Profiler::~Profiler() {
+    if (dump) fclose(dump);
+    for (auto e : pool) cudaEventDestroy(e);
+}
+
+void DeviceNetwork::set_host(const std::vector<TensorDef> &ts, int nv) {
     release();
     nvars = nv;
     offset.resize(ts.size());
     labels.resize(ts.size());
-    std::vector<int32_t> all;
+    host_vals.clear();
     for (size_t i = 0; i < ts.size(); i++) {
-        offset[i] = all.size();
+        offset[i] = host_vals.size();
         labels[i] = ts[i].labels;
-        all.insert(all.end(), ts[i].val.begin(), ts[i].val.end());
+        host_vals.insert(host_vals.end(), ts[i].val.begin(), ts[i].val.end());
     }
-    if (all.empty()) all.push_back(0);
-    BBTN_CUDA(cudaMalloc(&vals, all.size() * sizeof(int32_t)));
-    BBTN_CUDA(cudaMemcpyAsync(vals, all.data(), all.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (host_vals.empty()) host_vals.push_back(0);
+}
+
+void DeviceNetwork::upload(cudaStream_t s) {
+    if (vals) cudaFree(vals);
+    vals = nullptr;
+    BBTN_CUDA(cudaMalloc(&vals, host_vals.size() * sizeof(int32_t)));
+    BBTN_CUDA(cudaMemcpyAsync(vals, host_vals.data(), host_vals.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s));
     BBTN_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -162,6 +204,42 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
     post_order(t, order);
     const uint64_t elem = 4 + 8ull * np;
 
+    // Layout policy: each result orders its labels by the step at which they are
+    // next active (summed, or shared with the partner operand) -- latest first, so
+    // the low bits of a tensor are labels that its consumer passes through. The
+    // consumer's reads of its big operand then coalesce along those low bits.
+    std::vector<int> pos(t.nodes.size(), 0);
+    for (size_t i = 0; i < order.size(); i++) pos[order[i]] = (int)i;
+    std::vector<std::vector<int>> key(t.nodes.size());
+    {
+        std::vector<int> stack{t.root};
+        key[t.root].assign(t.nodes[t.root].lab.size(), (int)order.size());
+        while (!stack.empty()) {
+            const int q = stack.back();
+            stack.pop_back();
+            const CNode &nq = t.nodes[q];
+            if (nq.is_leaf()) continue;
+            for (int side = 0; side < 2; side++) {
+                const int a = side ? nq.r : nq.l, b = side ? nq.l : nq.r;
+                const auto &la = t.nodes[a].lab, &lb = t.nodes[b].lab;
+                key[a].resize(la.size());
+                for (size_t i = 0; i < la.size(); i++) {
+                    const int l = la[i];
+                    auto it = std::lower_bound(nq.lab.begin(), nq.lab.end(), l);
+                    const bool in_q = it != nq.lab.end() && *it == l;
+                    if (!in_q || std::binary_search(lb.begin(), lb.end(), l)) key[a][i] = pos[q];
+                    else key[a][i] = key[q][it - nq.lab.begin()];
+                }
+                stack.push_back(a);
+            }
+        }
+    }
+    auto key_of = [&](int node, int l) {
+        const auto &lab = t.nodes[node].lab;
+        auto it = std::lower_bound(lab.begin(), lab.end(), l);
+        return key[node][it - lab.begin()];
+    };
+
     auto leaf_view = [&](int id) {
         const CNode &nd = t.nodes[id];
         View v;
@@ -197,6 +275,9 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
         if (B)
             for (int l : B->bit_label)
                 if (l >= 0 && A->pos(l) < 0) (kept(l) ? out : sum).push_back(l);
+        if (!is_root)
+            std::stable_sort(out.begin(), out.end(),
+                             [&](int x, int y) { return key_of(id, x) > key_of(id, y); });
         if (out.size() > 30) fail(BBTN_ENOMEM, "intermediate rank above 30");
         if (sum.size() > 40) fail(BBTN_ENOMEM, "more than 40 summed labels in one step");
         PStep st;
@@ -306,8 +387,23 @@ void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *
             P.cc = (uint64_t *)(arena + ps.c.off + count_plane_offset_bytes(P.rc));
             P.planeC = 1ull << P.rc;
         }
+        Profiler *pr = st ? st->prof : nullptr;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (pr) {
+            ea = pr->get();
+            eb = pr->get();
+            BBTN_CUDA(cudaEventRecord(ea, s));
+        }
         cudaError_t e = launch_contract(P, s);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract kernel: ") + cudaGetErrorString(e));
+        if (pr) {
+            BBTN_CUDA(cudaEventRecord(eb, s));
+            int ra = 0, rb = 0, ident = 0;
+            for (int i = 0; i < P.rc; i++) { if (P.oA[i] >= 0) ra++; if (P.oB[i] >= 0) rb++; }
+            for (int j = 0; j < P.rs; j++) { if (P.sA[j] >= 0) ra++; if (P.sB[j] >= 0) rb++; }
+            while (ident < P.rc && P.oA[ident] == ident && P.oB[ident] < 0) ident++;
+            pr->recs.push_back({ea, eb, ps.bytes, ps.ops, ra, rb, P.rc, P.rs, ident, 0});
+        }
         if (st) st->launches++;
     }
     if (st) {

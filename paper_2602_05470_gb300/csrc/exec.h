@@ -19,7 +19,9 @@ struct DeviceNetwork {
     int32_t *vals = nullptr;                 // all tensors' values, concatenated
     std::vector<uint64_t> offset;            // element offset of tensor i
     std::vector<std::vector<int>> labels;    // bit i <-> labels[i]
-    void upload(const std::vector<TensorDef> &ts, int nvars, cudaStream_t s);
+    std::vector<int32_t> host_vals;          // staged values (set_host), uploaded by upload()
+    void set_host(const std::vector<TensorDef> &ts, int nvars);
+    void upload(cudaStream_t s);
     void release();
     ~DeviceNetwork() { release(); }
 };
@@ -64,9 +66,25 @@ uint64_t count_plane_offset_bytes(int r);
 Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
                const uint32_t *cprime, bool keep_all);
 
+// Per-launch CUDA-event timing of contraction kernels (profile mode): an event
+// pair on the launching stream around each launch, read back after a sync.
+struct Profiler {
+    struct Rec { cudaEvent_t a, b; double bytes, ops; int ra, rb, rc, rs, ident, kind; };
+    FILE *dump = nullptr;    // optional CSV of every launch (BBTN_PROFILE_DUMP)
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    size_t used = 0;
+    double ms = 0, bytes = 0, ops = 0, big_ms = 0, big_bytes = 0;
+    int64_t launches = 0, big_launches = 0;
+    cudaEvent_t get();
+    void collect();          // after the stream has been synchronised
+    ~Profiler();
+};
+
 struct RunStats {
     int64_t launches = 0;
     double ops = 0, bytes = 0;
+    Profiler *prof = nullptr;
 };
 
 // Enqueue a plan: arena = device base pointer of at least plan.arena_bytes,

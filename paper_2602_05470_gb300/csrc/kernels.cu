@@ -410,9 +410,18 @@ __global__ void k_fill(int32_t *val, uint64_t *cnt, uint64_t n, uint64_t plane, 
 
 }  // namespace
 
-cudaError_t launch_contract(const ContractParams &p, cudaStream_t s) {
+cudaError_t launch_contract_stream(const ContractParams &p, cudaStream_t s) {
     if (p.rc < 0 || p.rc > 30 || p.rs < 0 || p.rs > 40) return cudaErrorInvalidValue;
     return p.hasB ? dispatch_contract<true>(p, s) : dispatch_contract<false>(p, s);
+}
+
+cudaError_t launch_contract(const ContractParams &p, cudaStream_t s) {
+    if (p.rc < 0 || p.rc > 30 || p.rs < 0 || p.rs > 40) return cudaErrorInvalidValue;
+    if (p.hasB) {
+        cudaError_t e = launch_contract_tiled(p, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
+    return launch_contract_stream(p, s);
 }
 
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,

@@ -32,7 +32,13 @@ struct ContractParams {
     uint32_t cprime[kMaxPlanes];
 };
 
+// Picks the kernel: the register-tiled one (K1t) for large two-operand steps, else
+// the streaming gather kernel (K1 / K3).
 cudaError_t launch_contract(const ContractParams &p, cudaStream_t s);
+// K1t only; cudaErrorNotSupported when the step's shape does not fit it.
+cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s);
+// K1 / K3 only.
+cudaError_t launch_contract_stream(const ContractParams &p, cudaStream_t s);
 
 // out bit q <- in bit perm[q]
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,

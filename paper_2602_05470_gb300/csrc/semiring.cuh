@@ -34,6 +34,19 @@ __host__ __device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b, ui
     return z >= p ? z - p : z;
 }
 
+// x mod p for p = 2^61 - c, any x < 2^128 (same folding as mulmod61, one more round).
+__host__ __device__ __forceinline__ uint64_t reduce128_61(u128 x, uint32_t c) {
+    const uint64_t p = (1ull << 61) - c;
+    // x = q 2^61 + r, q < 2^67: fold q * c (< 2^77) + r, then as in mulmod61
+    u128 y = (u128)(uint64_t)(x >> 61) * (uint64_t)c + ((uint64_t)x & kM61) + ((u128)(uint64_t)(x >> 125) << 64) * c;
+    uint64_t r = (uint64_t)y & kM61;
+    u128 z = (u128)(uint64_t)(y >> 61) * (uint64_t)c + r;      // y >> 61 < 2^17
+    uint64_t zr = (uint64_t)z & kM61;
+    uint64_t zq = (uint64_t)(z >> 61);
+    uint64_t w = zr + zq * (uint64_t)c;
+    return w >= p ? w - p : w;
+}
+
 __host__ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b, uint32_t c) {
     const uint64_t p = (1ull << 61) - c;
     uint64_t s = a + b;                // < 2^62, no wrap

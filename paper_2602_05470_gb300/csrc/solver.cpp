@@ -4,6 +4,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <functional>
 
 #include "common.h"
@@ -135,6 +136,15 @@ void Solver::simplify(std::vector<int8_t> &fx) const {
 }
 
 void Solver::setup(const Problem &p, bool want_count) {
+    setup_host(p, want_count);
+    net_.upload(stream_);
+    release_buffers();
+    ensure_buffers(std::max(opts_.batch, 1) + 1);
+    cudaError_t e = launch_fill(d_val_, d_cnt_, 1, (uint64_t)dcap_ + 1, np_, kNeg, 0, stream_);
+    if (e != cudaSuccess) fail(BBTN_ECUDA, cudaGetErrorString(e));
+}
+
+void Solver::setup_host(const Problem &p, bool want_count) {
     p_ = &p;
     const auto &tab = prime_table();
     n_crt_ = want_count ? std::max(0, std::min(opts_.n_primes, BBTN_MAX_PRIMES)) : 0;
@@ -161,7 +171,7 @@ void Solver::setup(const Problem &p, bool want_count) {
     }
     simplify(fx0_);
 
-    net_.upload(build_network(p), p.n, stream_);
+    net_.set_host(build_network(p), p.n);
     const double t0 = now_s();
     const int cap = opts_.space_cap_log2;
     const double w_rho = opts_.mode == BBTN_MODE_PLAIN ? 8.0 : 1.0;
@@ -170,11 +180,6 @@ void Solver::setup(const Problem &p, bool want_count) {
     st_->tc_log2 = c.tc_log2;
     st_->sc_plain_log2 = c.sc;
     st_->t_plan_s += now_s() - t0;
-
-    release_buffers();
-    ensure_buffers(std::max(opts_.batch, 1) + 1);
-    cudaError_t e = launch_fill(d_val_, d_cnt_, 1, (uint64_t)dcap_ + 1, np_, kNeg, 0, stream_);
-    if (e != cudaSuccess) fail(BBTN_ECUDA, cudaGetErrorString(e));
     best_val_ = INT64_MIN;
     incumbent_ = INT64_MIN;
     best_fx_.clear();
@@ -182,10 +187,12 @@ void Solver::setup(const Problem &p, bool want_count) {
 }
 
 // Contract every leaf sub-network (each a full contraction of the network with its
-// fixed variables sliced out), then fold the results into the running
-// counting-sum in slot 0 (paper: the result is the sum over the branches).
-void Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves) {
-    if (leaves.empty()) return;
+// fixed variables sliced out). With counting, fold the results into the running
+// counting-sum in slot 0 (paper: the result is the sum over the branches);
+// without, only the leaves' maxima are computed (value planes only). Returns the
+// leaves' values.
+std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting) {
+    if (leaves.empty()) return {};
     const int64_t n = (int64_t)leaves.size();
     ensure_buffers(n + 1);   // slots 0..n, temporary at dcap_ > n
     const uint64_t plane = (uint64_t)dcap_ + 1;
@@ -195,25 +202,33 @@ void Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves) {
     BBTN_CUDA(cudaEventRecord(e0, stream_));
     const double tw = now_s();
     RunStats rs;
+    rs.prof = opts_.profile ? &prof_ : nullptr;
+    if (rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
+        prof_.dump = fopen(getenv("BBTN_PROFILE_DUMP"), "w");
+        if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms\n");
+    }
     for (int64_t i = 0; i < n; i++) {
         const double tp = now_s();
-        Plan plan = make_plan(tree_, net_, leaves[i], np_, cprime_, false);
+        Plan plan = make_plan(tree_, net_, leaves[i], counting ? np_ : 0, cprime_, false);
         st_->t_plan_s += now_s() - tp;
         arena_->reserve(plan.arena_bytes);
         st_->sc_log2 = std::max(st_->sc_log2, plan.max_rank);
         st_->steps += (int64_t)plan.steps.size();
         run_plan(plan, net_, arena_->ptr, d_val_ + 1 + i, d_cnt_ + 1 + i, plane, stream_, &rs);
     }
-    // slot 0 <- counting-sum of slots 0..n
-    int32_t *tv = d_val_ + dcap_;            // temporary result slot (last entry)
-    uint64_t *tc = d_cnt_ + dcap_;
-    cudaError_t e = launch_aggregate(n + 1, d_val_, d_cnt_, plane, np_, cprime_, tv, tc, plane, d_scratch_, stream_);
-    if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("aggregate: ") + cudaGetErrorString(e));
-    rs.launches += n + 1 > 256 ? 2 : 1;
-    BBTN_CUDA(cudaMemcpyAsync(d_val_, tv, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
-    for (int t = 0; t < np_; t++)
-        BBTN_CUDA(cudaMemcpyAsync(d_cnt_ + t * plane, tc + t * plane, sizeof(uint64_t),
-                                  cudaMemcpyDeviceToDevice, stream_));
+    if (counting) {
+        // slot 0 <- counting-sum of slots 0..n
+        int32_t *tv = d_val_ + dcap_;            // temporary result slot (last entry)
+        uint64_t *tc = d_cnt_ + dcap_;
+        cudaError_t e = launch_aggregate(n + 1, d_val_, d_cnt_, plane, np_, cprime_, tv, tc, plane, d_scratch_,
+                                         stream_);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("aggregate: ") + cudaGetErrorString(e));
+        rs.launches += n + 1 > 256 ? 2 : 1;
+        BBTN_CUDA(cudaMemcpyAsync(d_val_, tv, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
+        for (int t = 0; t < np_; t++)
+            BBTN_CUDA(cudaMemcpyAsync(d_cnt_ + t * plane, tc + t * plane, sizeof(uint64_t),
+                                      cudaMemcpyDeviceToDevice, stream_));
+    }
     std::vector<int32_t> vals(n);
     BBTN_CUDA(cudaMemcpyAsync(vals.data(), d_val_ + 1, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream_));
     BBTN_CUDA(cudaEventRecord(e1, stream_));
@@ -222,12 +237,22 @@ void Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves) {
     BBTN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rs.prof) {
+        prof_.collect();
+        st_->prof_ms = prof_.ms;
+        st_->prof_bytes = prof_.bytes;
+        st_->prof_ops = prof_.ops;
+        st_->prof_launches = prof_.launches;
+        st_->prof_big_ms = prof_.big_ms;
+        st_->prof_big_bytes = prof_.big_bytes;
+        st_->prof_big_launches = prof_.big_launches;
+    }
     st_->kernel_ms += ms;
     st_->t_device_s += now_s() - tw;
     st_->launches += rs.launches;
     st_->tropical_ops += rs.ops;
     st_->bytes_moved += rs.bytes;
-    st_->leaves += n;
+    if (counting) st_->leaves += n;
     for (int64_t i = 0; i < n; i++) {
         if (vals[i] >= kFiniteMin && vals[i] > best_val_) {
             best_val_ = vals[i];
@@ -235,6 +260,7 @@ void Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves) {
         }
         incumbent_ = std::max<int64_t>(incumbent_, vals[i] >= kFiniteMin ? vals[i] : INT64_MIN);
     }
+    return vals;
 }
 
 void Solver::run_plain() {
@@ -252,7 +278,7 @@ void Solver::run_sliced() {
     tree_ = t;
     st_->t_plan_s += now_s() - t0;
     st_->slices_log2 = (int)vf.size();
-    const int max_log2 = opts_.reserved[0] > 0 ? opts_.reserved[0] : 30;
+    const int max_log2 = opts_.max_slices_log2 > 0 ? opts_.max_slices_log2 : 30;
     if ((int)vf.size() > max_log2)
         fail(BBTN_ENOMEM, "slicing needs 2^" + std::to_string(vf.size()) + " slices");
     const uint64_t ns = 1ull << vf.size();
@@ -340,9 +366,21 @@ void Solver::run_bbtn() {
     std::vector<int> pow3(K + 1, 1);
     for (int i = 1; i <= K; i++) pow3[i] = pow3[i - 1] * 3;
 
+    // Two phases: every leaf is first contracted value-only (its maximum, which also
+    // raises the incumbent); only the leaves whose maximum equals the global optimum
+    // are contracted again with counts -- the others add nothing to the count.
+    std::vector<std::vector<int8_t>> cand;     // leaves that may attain the optimum
+    std::vector<int32_t> cand_val;
     while (!stack.empty() || !batch.empty()) {
         if (stack.empty() || (int)batch.size() >= bs) {
-            contract_leaves(batch);
+            std::vector<int32_t> v = contract_leaves(batch, np_ == 0);
+            if (np_ > 0) {
+                for (size_t i = 0; i < batch.size(); i++)
+                    if (v[i] >= kFiniteMin && v[i] >= incumbent_) {
+                        cand.push_back(std::move(batch[i]));
+                        cand_val.push_back(v[i]);
+                    }
+            }
             batch.clear();
             continue;
         }
@@ -557,6 +595,16 @@ void Solver::run_bbtn() {
         std::sort(kids.begin(), kids.end(), [](const BNode &a, const BNode &b) { return a.ub < b.ub; });
         for (auto &ch : kids) stack.push_back(std::move(ch));   // best bound popped first
     }
+    if (np_ > 0) {
+        std::vector<std::vector<int8_t>> opt;
+        for (size_t i = 0; i < cand.size(); i++)
+            if (cand_val[i] == incumbent_) opt.push_back(std::move(cand[i]));
+        st_->pruned += (int64_t)(cand.size() - opt.size());
+        for (size_t i = 0; i < opt.size(); i += (size_t)bs) {
+            std::vector<std::vector<int8_t>> b(opt.begin() + i, opt.begin() + std::min(opt.size(), i + (size_t)bs));
+            contract_leaves(b, true);
+        }
+    }
 }
 
 void Solver::finish(bool want_config) {
@@ -587,6 +635,52 @@ void Solver::finish(bool want_config) {
         if (objective(*p_, out_.x) != out_.value)
             fail(BBTN_ESTATE, "recovered configuration does not attain the optimum");
         out_.have_x = true;
+    }
+}
+
+void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path) {
+    bbtn_stats st;
+    memset(&st, 0, sizeof st);
+    st_ = &st;
+    setup_host(p, opts_.n_primes > 0);
+    memset(info, 0, sizeof(*info));
+    Cost c = tree_cost(tree_, opts_.space_cap_log2);
+    info->tc_log2 = c.tc_log2;
+    info->sc_log2 = c.sc;
+    info->rho = c.rho;
+    std::vector<int8_t> fx = fx0_;
+    if (opts_.mode == BBTN_MODE_SLICED) {
+        CTree t = tree_;
+        std::vector<int> vf = dynamic_slicing(t, opts_.space_cap_log2, std::max(1, opts_.sa_iters / 2), opts_.seed);
+        tree_ = t;
+        info->slices_log2 = (int)vf.size();
+        for (int v : vf) fx[v] = 0;
+    }
+    Plan plan = make_plan(tree_, net_, fx, np_, cprime_, false);
+    info->steps = (int64_t)plan.steps.size();
+    info->ops = plan.ops;
+    info->bytes = plan.bytes;
+    info->arena_bytes = (double)plan.arena_bytes;
+    if (dump_path) {
+        FILE *f = fopen(dump_path, "w");
+        if (!f) fail(BBTN_EIO, std::string("cannot write ") + dump_path);
+        fprintf(f, "rank_a,rank_b,rank_c,summed,low_identity_bits,bytes,ops,nb,nm,nn\n");
+        for (const PStep &ps : plan.steps) {
+            int ra = 0, rb = 0;
+            for (int i = 0; i < ps.P.rc; i++) { if (ps.P.oA[i] >= 0) ra++; if (ps.P.oB[i] >= 0) rb++; }
+            for (int j = 0; j < ps.P.rs; j++) { if (ps.P.sA[j] >= 0) ra++; if (ps.P.sB[j] >= 0) rb++; }
+            int ident = 0;
+            while (ident < ps.P.rc && ps.P.oA[ident] == ident && ps.P.oB[ident] < 0) ident++;
+            int nb = 0, nm = 0, nn = 0;
+            for (int i = 0; i < ps.P.rc; i++) {
+                if (ps.P.oA[i] >= 0 && ps.P.oB[i] >= 0) nb++;
+                else if (ps.P.oA[i] >= 0) nm++;
+                else nn++;
+            }
+            fprintf(f, "%d,%d,%d,%d,%d,%.0f,%.0f,%d,%d,%d\n", ra, rb, ps.P.rc, ps.P.rs, ident, ps.bytes, ps.ops, nb,
+                    nm, nn);
+        }
+        fclose(f);
     }
 }
 

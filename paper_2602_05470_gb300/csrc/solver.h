@@ -28,11 +28,14 @@ class Solver {
   public:
     Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena) : opts_(o), stream_(s), arena_(arena) {}
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
+    // host-only planning summary (bbtn_analyze)
+    void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);
 
   private:
     struct Leafset;
     void setup(const Problem &p, bool want_count);
-    void contract_leaves(const std::vector<std::vector<int8_t>> &leaves);
+    void setup_host(const Problem &p, bool want_count);
+    std::vector<int32_t> contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting = true);
     void finish(bool want_config);
     void run_plain();
     void run_sliced();
@@ -65,6 +68,7 @@ class Solver {
     int64_t incumbent_ = INT64_MIN;
     bbtn_stats *st_ = nullptr;
     SolveOutput out_;
+    Profiler prof_;
     void ensure_buffers(int64_t n);
     void release_buffers();
 };

@@ -1,0 +1,267 @@
+// K1t: register-tiled counting max-plus batched GEMM for pairwise steps whose two
+// operands are both large (paper Eq. (2); one binary step of contract(T)).
+//
+//   C[b, m, n] = max(NEG, max_k A[b, m, k] + B[b, k, n])
+//   cC_t[b, m, n] = sum over maximising k of cA_t * cB_t   (mod p_t)
+//
+// b, m, n, k are groups of binary labels (batch / A-only / B-only / summed); every
+// group is gathered through bit-deposit tables, so no permutation pass runs in front
+// of the step. A block computes a 64 x 64 output tile of one batch entry, 256
+// threads with a 4 x 4 micro-tile each, streaming K through shared memory in
+// chunks of 16. Pass 1 finds the maxima (int32 add + max, no tensor cores: max-plus
+// is not an MMA); pass 2 re-streams K and accumulates the count products of the
+// entries that attain the maximum.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace bbtn {
+
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int kThr = 256;
+
+struct Groups {
+    int nb, nm, nn, nk;
+    int8_t bA[30], bB[30], bC[30];
+    int8_t mA[30], mC[30];
+    int8_t nB[30], nC[30];
+    int8_t kA[30], kB[30];
+};
+
+__device__ __forceinline__ uint64_t deposit(uint64_t x, const int8_t *pos, int n) {
+    uint64_t r = 0;
+    for (int j = 0; j < n; j++)
+        if ((x >> j) & 1) r += (pos[j] >= 0) ? (1ull << pos[j]) : 0ull;
+    return r;
+}
+
+// load a TM x TK tile of A (rows m, columns k) into smem as [k][m]
+template <bool VALS, int NP>
+__device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
+                                          uint64_t plane, int unit, uint64_t base, const uint32_t *rowoff,
+                                          const uint32_t *koff, int k0, int fast_k, int32_t (*sv)[TM + 4],
+                                          uint64_t (*sc)[TK][TM + 2]) {
+    // 1024 elements, 4 per thread; lanes run along the operand's contiguous group
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int e = threadIdx.x + r * kThr;
+        int mi, ki;
+        if (fast_k) { ki = e & (TK - 1); mi = e >> 4; }
+        else { mi = e & (TM - 1); ki = e >> 6; }
+        const uint64_t off = base + rowoff[mi] + koff[k0 + ki];
+        const int32_t x = __ldg(v + off);
+        if (VALS) sv[ki][mi] = x;
+        if constexpr (NP > 0) {
+#pragma unroll
+            for (int t = 0; t < NP; t++)
+                sc[t][ki][mi] = unit ? (x >= kFiniteMin ? 1ull : 0ull) : __ldg(c + (uint64_t)t * plane + off);
+            sv[ki][mi] = x;
+        }
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThr, 1)
+k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups G, int fastA_k, int fastB_k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: koffA[K], koffB[K], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4], sB[TK][TN+4], counts
+    const int K = 1 << G.nk;
+    uint32_t *koffA = (uint32_t *)smem_raw;
+    uint32_t *koffB = koffA + K;
+    uint32_t *rowA = koffB + K;
+    uint32_t *colB = rowA + TM;
+    uint32_t *rowC = colB + TN;
+    uint32_t *colC = rowC + TM;
+    int32_t(*sA)[TM + 4] = (int32_t(*)[TM + 4])(colC + TN);
+    int32_t(*sB)[TN + 4] = (int32_t(*)[TN + 4])((int32_t *)sA + TK * (TM + 4));
+    uint64_t(*cA)[TK][TM + 2] = (uint64_t(*)[TK][TM + 2])(((uintptr_t)((int32_t *)sB + TK * (TN + 4)) + 15) & ~(uintptr_t)15);
+    uint64_t(*cB)[TK][TN + 2] = (uint64_t(*)[TK][TN + 2])((uint64_t *)cA + (NP > 0 ? NP : 1) * TK * (TM + 2));
+
+    const int mt = 1 << (G.nm > 6 ? G.nm - 6 : 0);
+    const int nt = 1 << (G.nn > 6 ? G.nn - 6 : 0);
+    const uint64_t tile = blockIdx.x;
+    const int tn = (int)(tile % nt);
+    const int tm = (int)((tile / nt) % mt);
+    const uint64_t b = tile / ((uint64_t)nt * mt);
+    const uint64_t baseA = P.A.base + deposit(b, G.bA, G.nb);
+    const uint64_t baseB = P.B.base + deposit(b, G.bB, G.nb);
+    const uint64_t baseC = deposit(b, G.bC, G.nb);
+    for (int i = threadIdx.x; i < K; i += kThr) {
+        koffA[i] = (uint32_t)deposit(i, G.kA, G.nk);
+        koffB[i] = (uint32_t)deposit(i, G.kB, G.nk);
+    }
+    for (int i = threadIdx.x; i < TM; i += kThr) {
+        const uint64_t m = (uint64_t)tm * TM + i;
+        rowA[i] = (uint32_t)deposit(m, G.mA, G.nm);
+        rowC[i] = (uint32_t)deposit(m, G.mC, G.nm);
+    }
+    for (int i = threadIdx.x; i < TN; i += kThr) {
+        const uint64_t n = (uint64_t)tn * TN + i;
+        colB[i] = (uint32_t)deposit(n, G.nB, G.nn);
+        colC[i] = (uint32_t)deposit(n, G.nC, G.nn);
+    }
+    __syncthreads();
+
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 each
+    int32_t best[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) best[i][j] = kNeg;
+
+    if constexpr (NP == 0) {
+        // values only: one pass of int32 add + max
+        for (int k0 = 0; k0 < K; k0 += TK) {
+            load_tile<true, 0>(P.A.val, nullptr, 0, 0, baseA, rowA, koffA, k0, fastA_k, sA, nullptr);
+            load_tile<true, 0>(P.B.val, nullptr, 0, 0, baseB, colB, koffB, k0, fastB_k, sB, nullptr);
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < TK; kk++) {
+                const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
+                const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+                const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) best[i][j] = __viaddmax_s32(a[i], bb[j], best[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) P.vc[baseC + rowC[ty * 4 + i] + colC[tx * 4 + j]] = best[i][j];
+    } else {
+        // values and counts in one pass over K. Per chunk: the chunk maximum of each
+        // output; a larger one restarts the count, an equal one adds the products of
+        // the chunk's maximising k (summed as 128-bit integers, reduced once).
+        uint64_t acc[4][4][NP];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
+        for (int k0 = 0; k0 < K; k0 += TK) {
+            load_tile<true, NP>(P.A.val, P.A.cnt, P.A.plane, P.A.unit_counts, baseA, rowA, koffA, k0, fastA_k,
+                                sA, cA);
+            load_tile<true, NP>(P.B.val, P.B.cnt, P.B.plane, P.B.unit_counts, baseB, colB, koffB, k0, fastB_k,
+                                sB, cB);
+            __syncthreads();
+            int32_t cm[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) cm[i][j] = kNeg;
+#pragma unroll
+            for (int kk = 0; kk < TK; kk++) {
+                const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
+                const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+                const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) cm[i][j] = __viaddmax_s32(a[i], bb[j], cm[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (cm[i][j] > best[i][j]) {
+                        best[i][j] = cm[i][j];
+#pragma unroll
+                        for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
+                    }
+                    if (cm[i][j] == best[i][j] && cm[i][j] >= kFiniteMin) {
+                        u128 part[NP];
+#pragma unroll
+                        for (int t = 0; t < NP; t++) part[t] = 0;
+                        const int mi = ty * 4 + i, nj = tx * 4 + j;
+                        for (int kk = 0; kk < TK; kk++) {
+                            if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+#pragma unroll
+                            for (int t = 0; t < NP; t++) part[t] += (u128)cA[t][kk][mi] * cB[t][kk][nj];
+                        }
+#pragma unroll
+                        for (int t = 0; t < NP; t++)
+                            acc[i][j][t] = addmod61(acc[i][j][t], reduce128_61(part[t], P.cprime[t]), P.cprime[t]);
+                    }
+                }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t o = baseC + rowC[ty * 4 + i] + colC[tx * 4 + j];
+                P.vc[o] = best[i][j];
+#pragma unroll
+                for (int t = 0; t < NP; t++) P.cc[(uint64_t)t * P.planeC + o] = acc[i][j][t];
+            }
+    }
+}
+
+size_t tiled_smem(int nk, int np) {
+    const size_t K = (size_t)1 << nk;
+    size_t s = 2 * K * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
+    const int planes = np > 0 ? np : 1;
+    s += (size_t)planes * TK * (TM + 2) * 8 + (size_t)planes * TK * (TN + 2) * 8;
+    return s;
+}
+
+template <int NP>
+cudaError_t launch_t(const ContractParams &p, const Groups &g, int fa, int fb, cudaStream_t s) {
+    const size_t smem = tiled_smem(g.nk, NP);
+    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t blocks = (1ull << g.nb) * (1ull << (g.nm - 6)) * (1ull << (g.nn - 6));
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    k_tiled<NP><<<(unsigned)blocks, kThr, smem, s>>>(p, g, fa, fb);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Decide whether a step fits the tiled kernel and, if so, launch it.
+// Returns cudaErrorNotSupported when the step has to take the streaming kernel.
+cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
+    if (!p.hasB || p.np > 4) return cudaErrorNotSupported;
+    Groups g{};
+    int bitA0 = -1, bitB0 = -1;   // which group holds bit 0 of A / B
+    for (int i = 0; i < p.rc; i++) {
+        const int a = p.oA[i], b = p.oB[i];
+        if (a >= 0 && b >= 0) {
+            g.bA[g.nb] = (int8_t)a; g.bB[g.nb] = (int8_t)b; g.bC[g.nb] = (int8_t)i; g.nb++;
+        } else if (a >= 0) {
+            if (a == 0) bitA0 = 1;
+            g.mA[g.nm] = (int8_t)a; g.mC[g.nm] = (int8_t)i; g.nm++;
+        } else {
+            if (b == 0) bitB0 = 1;
+            g.nB[g.nn] = (int8_t)b; g.nC[g.nn] = (int8_t)i; g.nn++;
+        }
+    }
+    for (int j = 0; j < p.rs; j++) {
+        if (p.sA[j] == 0) bitA0 = 0;
+        if (p.sB[j] == 0) bitB0 = 0;
+        g.kA[g.nk] = p.sA[j];
+        g.kB[g.nk] = p.sB[j];
+        g.nk++;
+    }
+    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 13) return cudaErrorNotSupported;
+    // lanes along k when the operand's bit 0 is a summed label, else along m / n
+    const int fa = bitA0 == 0, fb = bitB0 == 0;
+    switch (p.np) {
+        case 0: return launch_t<0>(p, g, fa, fb, s);
+        case 1: return launch_t<1>(p, g, fa, fb, s);
+        case 2: return launch_t<2>(p, g, fa, fb, s);
+        case 3: return launch_t<3>(p, g, fa, fb, s);
+        case 4: return launch_t<4>(p, g, fa, fb, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace bbtn

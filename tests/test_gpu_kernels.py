@@ -85,6 +85,63 @@ def test_contract_parity(P, case, np_):
     assert np.array_equal(cc, oc)
 
 
+def _labels(prefix_ids):
+    return list(prefix_ids)
+
+
+# shapes that take the register-tiled kernel: >= 6 A-only and B-only labels and
+# 4..13 summed labels; label ids: m 0-9, n 10-19, k 20-33, batch 40-43
+TILED = [
+    # (m, n, k, batch, A's first group, B's first group, C order)
+    (6, 6, 4, 1, "m", "k", "mnb"),
+    (6, 6, 4, 1, "k", "n", "nmb"),
+    (7, 6, 6, 2, "k", "k", "bnm"),
+    (6, 7, 5, 0, "m", "n", "mn"),
+    (6, 6, 8, 0, "k", "k", "nm"),
+]
+
+
+def _tiled_case(m, n, k, b, afirst, bfirst, corder, private=False):
+    M = list(range(0, m))
+    N = list(range(10, 10 + n))
+    K = list(range(20, 20 + k))
+    Bt = list(range(40, 40 + b))
+    la = (K + M + Bt) if afirst == "k" else (M + K + Bt)
+    lb = (K + N + Bt) if bfirst == "k" else (N + K + Bt)
+    if private:
+        lb = lb + [50]               # summed label private to B
+    groups = {"m": M, "n": N, "b": Bt}
+    lc = [x for g in corder for x in groups[g]]
+    return la, lb, lc
+
+
+@pytest.mark.parametrize("case", range(len(TILED)))
+@pytest.mark.parametrize("np_", [0, 1, 3])
+def test_contract_tiled_parity(P, case, np_):
+    la, lb, lc = _tiled_case(*TILED[case])
+    rng = np.random.default_rng(500 + case)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), -4, 4, neg_frac=0.05)
+    B = _rand(rng, len(lb), max(np_, 1), -4, 4, neg_frac=0.05)
+    A = (A[0], A[1][:np_])
+    B = (B[0], B[1][:np_])
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov)
+    assert np.array_equal(cc, oc)
+
+
+def test_contract_tiled_private_label(P):
+    la, lb, lc = _tiled_case(6, 6, 4, 0, "m", "k", "mn", private=True)
+    rng = np.random.default_rng(77)
+    primes = P.primes(3)
+    A = _rand(rng, len(la), 3, -2, 2)
+    B = _rand(rng, len(lb), 3, -2, 2)
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
 @pytest.mark.parametrize("np_", [2, 8, 9])
 def test_contract_many_planes(P, np_):
     la, lb, lc = [0, 1, 2, 3, 4], [3, 4, 5, 6], [0, 1, 2, 5, 6]
