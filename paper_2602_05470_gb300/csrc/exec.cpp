@@ -192,6 +192,140 @@ void Arena::release() {
     owned = true;
 }
 
+// Marks the small subtrees that run fused (every step with at most 2^S outputs and
+// its intermediates fitting in shared memory), lays out their shared memory, and
+// assigns arena blocks in execution order: fused results first, then the other
+// steps in post-order, each block released after its last reader is enqueued.
+static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, FreeList &fl) {
+    const int nsteps = (int)plan.steps.size();
+    std::vector<char> fus(t.nodes.size(), 0);
+    const int S = np == 0 ? 12 : 10;
+    const uint64_t budget = 200 * 1024;
+    if (!keep_all && np <= 4) {
+        for (int i = 0; i < nsteps; i++) {
+            const PStep &ps = plan.steps[i];
+            if (t.nodes[ps.node].is_leaf()) continue;
+            bool ok = ps.P.rc <= S && ps.P.rs <= 12;
+            for (int c : {ps.a_node, ps.b_node})
+                if (c >= 0 && !t.nodes[c].is_leaf() && !fus[c]) ok = false;
+            fus[ps.node] = ok;
+        }
+    }
+    auto nint = [&](int n) {   // internal nodes of a fused subtree
+        int c = 0;
+        std::vector<int> st{n};
+        while (!st.empty()) {
+            int x = st.back();
+            st.pop_back();
+            if (t.nodes[x].is_leaf()) continue;
+            c++;
+            st.push_back(t.nodes[x].l);
+            st.push_back(t.nodes[x].r);
+        }
+        return c;
+    };
+    std::vector<int> roots;
+    std::vector<uint32_t> soff(t.nodes.size(), 0);
+    for (bool changed = true; changed;) {
+        changed = false;
+        roots.clear();
+        for (int i = 0; i < nsteps; i++) {
+            const int n = plan.steps[i].node;
+            const int par = t.nodes[n].parent;
+            if (fus[n] && (par < 0 || !fus[par])) roots.push_back(n);
+        }
+        plan.fused_smem = 0;
+        for (int r : roots) {
+            const int last = plan.node_step[r], first = last - nint(r) + 1;
+            FreeList fsm;
+            for (int i = first; i <= last; i++) {
+                const PStep &ps = plan.steps[i];
+                if (ps.node != r) soff[ps.node] = (uint32_t)fsm.alloc(smem_tensor_bytes(ps.P.rc, np));
+                for (int c : {ps.a_node, ps.b_node})
+                    if (c >= 0 && !t.nodes[c].is_leaf())
+                        fsm.release(soff[c], smem_tensor_bytes(plan.steps[plan.node_step[c]].P.rc, np));
+            }
+            if (fsm.peak > budget) {
+                fus[r] = 0;
+                changed = true;
+            }
+            plan.fused_smem = std::max<size_t>(plan.fused_smem, fsm.peak);
+        }
+    }
+    // arena: fused results are alive from the fused launch on
+    for (int r : roots)
+        if (r != t.root) {
+            PStep &ps = plan.steps[plan.node_step[r]];
+            ps.c.off = fl.alloc(ps.c_block);
+        }
+    for (int i = 0; i < nsteps; i++) {
+        PStep &ps = plan.steps[i];
+        if (fus[ps.node]) {
+            ps.fused = true;
+            continue;
+        }
+        if (ps.c.kind == 1) ps.c.off = fl.alloc(ps.c_block);
+        for (int side = 0; side < 2; side++) {
+            const int c = side ? ps.b_node : ps.a_node;
+            if (c < 0 || t.nodes[c].is_leaf() || (side == 1 && !ps.P.hasB)) continue;
+            const PStep &cs = plan.steps[plan.node_step[c]];
+            (side ? ps.b : ps.a) = cs.c;
+            if (!keep_all) fl.release(cs.c.off, cs.c_block);
+        }
+    }
+    plan.arena_bytes = fl.peak;
+    // the fused program
+    for (int r : roots) {
+        const int last = plan.node_step[r], first = last - nint(r) + 1;
+        FSub sub;
+        sub.first = (int)plan.fsteps.size();
+        sub.count = last - first + 1;
+        for (int i = first; i <= last; i++) {
+            const PStep &ps = plan.steps[i];
+            FStep f;
+            memset(&f, 0, sizeof f);
+            f.rc = (int8_t)ps.P.rc;
+            f.rs = (int8_t)ps.P.rs;
+            f.hasB = (int8_t)ps.P.hasB;
+            for (int q = 0; q < kFusedMaxBits; q++) {
+                f.oA[q] = ps.P.oA[q];
+                f.oB[q] = ps.P.oB[q];
+                f.sA[q] = ps.P.sA[q];
+                f.sB[q] = ps.P.sB[q];
+            }
+            for (int side = 0; side < 2; side++) {
+                const int c = side ? ps.b_node : ps.a_node;
+                if (side == 1 && !ps.P.hasB) continue;
+                const Ref &rf = side ? ps.b : ps.a;
+                int8_t kind, rank = 0;
+                uint32_t off;
+                if (c < 0 || t.nodes[c].is_leaf()) {
+                    kind = 0;
+                    off = (uint32_t)(rf.off + rf.base);
+                } else {
+                    kind = 1;
+                    off = soff[c];
+                    rank = (int8_t)plan.steps[plan.node_step[c]].P.rc;
+                }
+                if (side) { f.b_kind = kind; f.b_off = off; f.b_rank = rank; }
+                else { f.a_kind = kind; f.a_off = off; f.a_rank = rank; }
+            }
+            if (ps.node != r) {
+                f.c_kind = 1;
+                f.c_off = soff[ps.node];
+            } else if (r == t.root) {
+                f.c_kind = 3;
+            } else {
+                f.c_kind = 2;
+                f.c_goff = ps.c.off;
+            }
+            plan.fsteps.push_back(f);
+            plan.fused_steps++;
+        }
+        plan.fsubs.push_back(sub);
+    }
+}
+
 Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
                const uint32_t *cprime, bool keep_all) {
     Plan plan;
@@ -314,7 +448,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
         } else {
             C.ref.kind = 1;
             C.block_bytes = block_bytes(P.rc, np);
-            C.ref.off = fl.alloc(C.block_bytes);
+            C.ref.off = 0;                     // assigned by the allocation pass below
             C.ref.plane = 1ull << P.rc;
             C.ref.rank = P.rc;
         }
@@ -326,11 +460,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
         plan.ops += st.ops;
         plan.bytes += st.bytes;
         plan.max_rank = std::max(plan.max_rank, P.rc);
-        // operands are no longer needed once this step is enqueued
-        if (!keep_all) {
-            if (X->ref.kind == 1) fl.release(X->ref.off, X->block_bytes);
-            if (Y && Y->ref.kind == 1) fl.release(Y->ref.off, Y->block_bytes);
-        }
+        st.c_block = C.block_bytes;
         plan.node_step[id] = (int)plan.steps.size();
         plan.node_layout[id] = out;
         plan.steps.push_back(st);
@@ -350,7 +480,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
             view[nd.r].bit_label.clear();
         }
     }
-    plan.arena_bytes = fl.peak;
+    finalize_plan(plan, t, np, keep_all, fl);
     return plan;
 }
 
@@ -368,9 +498,58 @@ static void fill_operand(Operand &o, const Ref &r, const DeviceNetwork &net, cha
     }
 }
 
+void DeviceBuf::reserve(size_t bytes) {
+    if (bytes <= size) return;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    size = 0;
+    const size_t want = std::max(bytes * 2, (size_t)1 << 20);
+    BBTN_CUDA(cudaMalloc(&ptr, want));
+    size = want;
+}
+
+DeviceBuf::~DeviceBuf() {
+    if (ptr) cudaFree(ptr);
+}
+
 void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
-              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st) {
+              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st, DeviceBuf *prog) {
+    if (!plan.fsubs.empty()) {
+        // all small subtrees in one launch; their results precede every other step
+        const size_t bs = plan.fsteps.size() * sizeof(FStep);
+        const size_t bsub = plan.fsubs.size() * sizeof(FSub);
+        const size_t off_sub = (bs + 255) & ~(size_t)255;
+        prog->reserve(off_sub + bsub);
+        BBTN_CUDA(cudaMemcpyAsync(prog->ptr, plan.fsteps.data(), bs, cudaMemcpyHostToDevice, s));
+        BBTN_CUDA(cudaMemcpyAsync((char *)prog->ptr + off_sub, plan.fsubs.data(), bsub, cudaMemcpyHostToDevice, s));
+        FusedParams fp{};
+        fp.steps = (const FStep *)prog->ptr;
+        fp.subs = (const FSub *)((char *)prog->ptr + off_sub);
+        fp.nsubs = (int)plan.fsubs.size();
+        fp.net = net.vals;
+        fp.arena = arena;
+        fp.out_val = out_val;
+        fp.out_cnt = out_cnt;
+        fp.out_plane = out_plane;
+        fp.np = plan.np;
+        for (int t2 = 0; t2 < plan.np; t2++) fp.cprime[t2] = plan.steps.empty() ? 0 : plan.steps[0].P.cprime[t2];
+        Profiler *pr = st ? st->prof : nullptr;
+        cudaEvent_t ea = nullptr, eb = nullptr;
+        if (pr) {
+            ea = pr->get();
+            eb = pr->get();
+            BBTN_CUDA(cudaEventRecord(ea, s));
+        }
+        cudaError_t e = launch_fused(fp, plan.fused_smem, s);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("fused kernel: ") + cudaGetErrorString(e));
+        if (pr) {
+            BBTN_CUDA(cudaEventRecord(eb, s));
+            pr->recs.push_back({ea, eb, 0.0, 0.0, 0, 0, 0, 0, 0, 1});
+        }
+        if (st) st->launches++;
+    }
     for (const PStep &ps : plan.steps) {
+        if (ps.fused) continue;
         ContractParams P = ps.P;
         fill_operand(P.A, ps.a, net, arena);
         P.A.unit_counts = ps.a.kind == 0;

@@ -43,6 +43,8 @@ struct PStep {
     int lab_c[32];         // output labels (bit order of C)
     double ops = 0;        // 2^{|union|} multiply-adds
     double bytes = 0;      // algorithmic bytes (operands read once, result written once)
+    uint64_t c_block = 0;  // arena bytes of the result (kind 1)
+    bool fused = false;    // runs inside a fused small-subtree block
 };
 
 struct Plan {
@@ -54,6 +56,11 @@ struct Plan {
     // per tree node: its step index (internal) and the bit order of its result
     std::vector<int> node_step;
     std::vector<std::vector<int>> node_layout;
+    // fused small subtrees (one launch before the remaining steps)
+    std::vector<FStep> fsteps;
+    std::vector<FSub> fsubs;
+    size_t fused_smem = 0;
+    int64_t fused_steps = 0;
 };
 
 // Element layout of an arena block of rank r with np count planes.
@@ -87,10 +94,19 @@ struct RunStats {
     Profiler *prof = nullptr;
 };
 
+// Grow-only device buffer for the fused-subtree programs.
+struct DeviceBuf {
+    void *ptr = nullptr;
+    size_t size = 0;
+    void reserve(size_t bytes);
+    ~DeviceBuf();
+};
+
 // Enqueue a plan: arena = device base pointer of at least plan.arena_bytes,
-// root result to (out_val[0], out_cnt[t * out_plane]).
+// root result to (out_val[0], out_cnt[t * out_plane]); prog holds the fused
+// program while it runs (stream-ordered reuse across plans).
 void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
-              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st);
+              uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st, DeviceBuf *prog);
 
 // Backward walk after run_plan with keep_all: sets x[v] for every free variable
 // (fixed ones copied from fx). Synchronises the stream.

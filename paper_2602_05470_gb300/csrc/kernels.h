@@ -52,6 +52,41 @@ cudaError_t launch_aggregate(int64_t n, const int32_t *vals, const uint64_t *cnt
                              int np, const uint32_t *cprime, int32_t *out_val, uint64_t *out_cnt,
                              uint64_t out_plane, void *scratch, cudaStream_t s);
 
+// K5: small subtrees of a contraction tree run by one thread block each, with every
+// intermediate in shared memory and only the subtree's result written to global
+// memory. One launch runs all subtrees of a plan.
+constexpr int kFusedMaxBits = 16;      // output / summed bits of a fused step
+struct FStep {
+    int8_t rc, rs, hasB;
+    int8_t a_kind, b_kind;             // 0: network tensor (global, unit counts), 1: shared memory
+    int8_t c_kind;                     // 1: shared memory, 2: arena block, 3: external result
+    int8_t a_rank, b_rank;             // ranks of shared-memory operands (plane stride 2^rank)
+    int8_t oA[kFusedMaxBits], oB[kFusedMaxBits], sA[kFusedMaxBits], sB[kFusedMaxBits];
+    uint32_t a_off, b_off, c_off;      // network: element offset (base included); smem: byte offset
+    uint64_t c_goff;                   // arena byte offset (c_kind 2)
+};
+struct FSub {
+    int first, count;                  // its steps, in post-order
+};
+struct FusedParams {
+    const FStep *steps;
+    const FSub *subs;
+    int nsubs;
+    const int32_t *net;
+    char *arena;
+    int32_t *out_val;
+    uint64_t *out_cnt;
+    uint64_t out_plane;
+    int np;
+    uint32_t cprime[kMaxPlanes];
+};
+// byte offset of the count planes inside a shared-memory tensor of rank r
+__host__ __device__ inline uint32_t smem_count_offset(int r) { return ((4u << r) + 15u) & ~15u; }
+__host__ __device__ inline uint32_t smem_tensor_bytes(int r, int np) {
+    return smem_count_offset(r) + (uint32_t)np * (8u << r);
+}
+cudaError_t launch_fused(const FusedParams &p, size_t smem_bytes, cudaStream_t s);
+
 // Tropical argmax of one step for q selected outputs (values only).
 struct BackwardParams {
     const int32_t *va = nullptr, *vb = nullptr, *vc = nullptr;

@@ -214,7 +214,7 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
         arena_->reserve(plan.arena_bytes);
         st_->sc_log2 = std::max(st_->sc_log2, plan.max_rank);
         st_->steps += (int64_t)plan.steps.size();
-        run_plan(plan, net_, arena_->ptr, d_val_ + 1 + i, d_cnt_ + 1 + i, plane, stream_, &rs);
+        run_plan(plan, net_, arena_->ptr, d_val_ + 1 + i, d_cnt_ + 1 + i, plane, stream_, &rs, &prog_);
     }
     if (counting) {
         // slot 0 <- counting-sum of slots 0..n
@@ -628,7 +628,7 @@ void Solver::finish(bool want_config) {
         arena_->reserve(plan.arena_bytes);
         int32_t *root = d_val_ + dcap_;
         RunStats rs;
-        run_plan(plan, net_, arena_->ptr, root, nullptr, 0, stream_, &rs);
+        run_plan(plan, net_, arena_->ptr, root, nullptr, 0, stream_, &rs, &prog_);
         backward_config(plan, tree_, net_, arena_->ptr, root, best_fx_, out_.x, stream_);
         st_->launches += rs.launches + (int64_t)plan.steps.size();
         for (auto &xv : out_.x) if (xv < 0) xv = 0;   // variables absent from every tensor

@@ -69,6 +69,7 @@ class Solver {
     bbtn_stats *st_ = nullptr;
     SolveOutput out_;
     Profiler prof_;
+    DeviceBuf prog_;                    // fused-subtree programs
     void ensure_buffers(int64_t n);
     void release_buffers();
 };
