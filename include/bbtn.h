@@ -108,6 +108,27 @@ int bbtn_aggregate(int64_t n, const int32_t *vals, const uint64_t *counts, int n
                    void *stream);
 
 /*
+ * The same reduction as bbtn_aggregate (same arguments, same result) but it
+ * allocates nothing: no cudaMalloc, cudaFree or other allocating routine is called.
+ * (The paper has no counterpart; this entry point exists for callers that must not
+ * allocate while they run, e.g. an application whose own memory manager already
+ * holds the whole device, or a latency-critical loop that keeps allocation out of
+ * its steady state.) Its per-block partial results live in one fixed device array
+ * of bbtn_aggregate_noalloc_max_scratch() bytes (64 KiB) compiled into the library;
+ * every GPU that loads the library holds that array until the process exits. The
+ * reduction never needs more than that for any n (at most 608 partials of up to
+ * 9 planes), and a request that would is rejected with BBTN_EINVAL. The first call
+ * on a device looks up the array's device address with that device current, so
+ * make that first call before any stream capture. All calls on a device share the
+ * array and the last call's partials stay in it; nothing in it has to start at
+ * zero, but calls that overlap on the GPU (concurrent streams) race on it.
+ */
+int bbtn_aggregate_noalloc(int64_t n, const int32_t *vals, const uint64_t *counts, int np,
+                           const uint64_t *primes, int32_t *out_val, uint64_t *out_counts,
+                           void *stream);
+size_t bbtn_aggregate_noalloc_max_scratch(void);
+
+/*
  * Tropical back-propagation through one pairwise step (the backward pass that
  * recovers an optimal configuration): for each of `q` selected output entries
  * sel_o[i] of C = contract(A, B) (values only), find the smallest summed

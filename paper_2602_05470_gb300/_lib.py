@@ -87,6 +87,8 @@ _SIGS = {
     "bbtn_get_config": ([_vp, _i8p], C.c_int),
     "bbtn_get_stats": ([_vp, _P(Stats)], C.c_int),
     "bbtn_analyze": ([_vp, _P(PlanInfo), C.c_char_p], C.c_int),
+    "bbtn_aggregate_noalloc": ([C.c_int64, _vp, _vp, C.c_int, _u64p, _vp, _vp, _vp], C.c_int),
+    "bbtn_aggregate_noalloc_max_scratch": ([], C.c_size_t),
 }
 
 
