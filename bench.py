@@ -181,9 +181,10 @@ def run_ours(args, rank, world, local_rank):
 
     for w in range(args.warmup):
         one_step(w + 1000, False)
-    clocks = Clocks(local_rank)
+    clocks = Clocks(local_rank) if not args.no_clocks else None
     tot_dev, tot_wall, stats, H2D, D2H = 0.0, 0.0, {}, 0, 0
-    clocks.start()
+    if clocks:
+        clocks.start()
     for s in range(args.steps):
         flush.fill_(s)                                    # evict L2 between timed steps
         if dist:
@@ -197,7 +198,7 @@ def run_ours(args, rank, world, local_rank):
         D2H += d2h
         for k, v in st.items():
             stats[k] = stats.get(k, 0) + v
-    ck = clocks.stop()
+    ck = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
     if dist:
         t = torch.tensor([tot_dev, tot_wall], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -205,13 +206,14 @@ def run_ours(args, rank, world, local_rank):
     n_inst = per * args.steps * world
     # roofline: one more pass over step 0's instances with every contraction launch
     # bracketed by CUDA events on this stream (not part of the timed region)
-    prof = make_solver(profile=True)
     pb = {"prof_ms": 0.0, "prof_bytes": 0.0, "prof_big_ms": 0.0, "prof_big_bytes": 0.0,
           "prof_launches": 0, "prof_big_launches": 0, "prof_ops": 0.0}
-    for _, inst in instances(rank, world, 0, per):
-        r = prof.solve(inst, count=True, config=False)
-        for k in pb:
-            pb[k] += r.stats[k]
+    if not args.no_profile_pass:
+        prof = make_solver(profile=True)
+        for _, inst in instances(rank, world, 0, per):
+            r = prof.solve(inst, count=True, config=False)
+            for k in pb:
+                pb[k] += r.stats[k]
     peak, peak_kind = measured_peaks()
     big_gbs = pb["prof_big_bytes"] / (pb["prof_big_ms"] * 1e6) if pb["prof_big_ms"] else 0.0
     all_gbs = pb["prof_bytes"] / (pb["prof_ms"] * 1e6) if pb["prof_ms"] else 0.0
@@ -244,8 +246,56 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+KERNEL_CASES = {
+    # name: (A labels, B labels, C labels, count planes); tiled: m 0-19, k 20-39, n 40-59, batch 60+
+    # streaming step: a rank-26 tensor absorbs an edge matrix, one label summed
+    "stream": ([200] + list(range(100, 125)), [200, 300], list(range(100, 125)) + [300], 0),
+    "stream_count": ([200] + list(range(100, 123)), [200, 300], list(range(100, 123)) + [300], 4),
+    # big x big step of the 30x30 workload: batch 2, m 11, n 11, k 10
+    "tiled": (list(range(0, 11)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 51)) + [60, 61],
+              list(range(0, 11)) + list(range(40, 51)) + [60, 61], 0),
+    "tiled_count": (list(range(0, 10)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 50)) + [60, 61],
+                    list(range(0, 10)) + list(range(40, 50)) + [60, 61], 4),
+}
+
+
+def run_kernel_case(args):
+    """One representative contraction step through the C ABI, timed with CUDA events."""
+    import torch
+    import paper_2602_05470_gb300 as P
+    la, lb, lc, np_ = KERNEL_CASES[args.kernel_case]
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    va = torch.randint(-4, 4, (1 << len(la),), dtype=torch.int32, device="cuda", generator=gen)
+    vb = torch.randint(-4, 4, (1 << len(lb),), dtype=torch.int32, device="cuda", generator=gen)
+    ca = torch.randint(0, 1 << 60, (np_, 1 << len(la)), dtype=torch.int64, device="cuda", generator=gen) if np_ else None
+    cb = torch.randint(0, 1 << 60, (np_, 1 << len(lb)), dtype=torch.int64, device="cuda", generator=gen) if np_ else None
+    primes = P.primes(np_)
+    out = (torch.empty(1 << len(lc), dtype=torch.int32, device="cuda"),
+           torch.empty((np_, 1 << len(lc)), dtype=torch.int64, device="cuda") if np_ else None)
+    for _ in range(args.warmup):
+        P.contract(la, va, ca, lb, vb, cb, lc, primes, out=out)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.steps):
+        P.contract(la, va, ca, lb, vb, cb, lc, primes, out=out)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    elem = 4 + 8 * np_
+    union = set(la) | set(lb)
+    byts = elem * (2 ** len(la) + 2 ** len(lb) + 2 ** len(lc))
+    ops = 2.0 ** len(union)
+    peak, kind = measured_peaks()
+    print(json.dumps({"kernel_case": args.kernel_case, "ms": ms, "algorithmic_bytes": byts, "tropical_ops": ops,
+                      "gbs": byts / ms / 1e6, "hbm_frac": byts / ms / 1e6 / peak, "tops": ops / ms / 1e9,
+                      "peak_gbs": peak, "peak_source": kind}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES), default=None,
+                    help="time one representative contraction step instead of the workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -253,13 +303,17 @@ def main():
     ap.add_argument("--instances-per-step", type=int, default=4)
     ap.add_argument("--cpu-instances", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
+    ap.add_argument("--no-profile-pass", action="store_true", help="skip the per-launch roofline pass")
     ap.add_argument("--check", action="store_true", help="compare step 0 with the stored oracle answers")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
-    if args.impl == "reference":
+    if args.kernel_case:
+        run_kernel_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     else:
         run_ours(args, rank, world, local_rank)
