@@ -8,9 +8,10 @@
 // group is gathered through bit-deposit tables, so no permutation pass runs in front
 // of the step. A block computes a 64 x 64 output tile of one batch entry, 256
 // threads with a 4 x 4 micro-tile each, streaming K through shared memory in
-// chunks of 16. Pass 1 finds the maxima (int32 add + max, no tensor cores: max-plus
-// is not an MMA); pass 2 re-streams K and accumulates the count products of the
-// entries that attain the maximum.
+// chunks of 16 (int32 add + max, no tensor cores: max-plus is not an MMA). Values
+// only: the next chunk is prefetched into registers while the current one is
+// computed. With counts: one pass in which each chunk's maximum either restarts an
+// output's count or adds the products of the chunk's maximising k.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -63,7 +64,7 @@ __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const u
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kThr, 1)
+__global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1)
 k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups G, int fastA_k, int fastB_k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // layout: koffA[K], koffB[K], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4], sB[TK][TN+4], counts
@@ -112,23 +113,48 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
         for (int j = 0; j < 4; j++) best[i][j] = kNeg;
 
     if constexpr (NP == 0) {
-        // values only: one pass of int32 add + max
-        for (int k0 = 0; k0 < K; k0 += TK) {
-            load_tile<true, 0>(P.A.val, nullptr, 0, 0, baseA, rowA, koffA, k0, fastA_k, sA, nullptr);
-            load_tile<true, 0>(P.B.val, nullptr, 0, 0, baseB, colB, koffB, k0, fastB_k, sB, nullptr);
-            __syncthreads();
+        // values only: int32 add + max. The next chunk's tiles are fetched into
+        // registers while the current chunk is computed from shared memory.
+        {
+            int32_t ra[4], rb[4];
+            auto gload = [&](int k0) {
 #pragma unroll
-            for (int kk = 0; kk < TK; kk++) {
-                const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
-                const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
-                const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-                const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+                for (int r = 0; r < 4; r++) {
+                    const int e = threadIdx.x + r * kThr;
+                    const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
+                    ra[r] = __ldg(P.A.val + baseA + rowA[mi] + koffA[k0 + ki]);
+                    const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
+                    rb[r] = __ldg(P.B.val + baseB + colB[nj] + koffB[k0 + kj]);
+                }
+            };
+            auto sstore = [&]() {
 #pragma unroll
-                for (int i = 0; i < 4; i++)
+                for (int r = 0; r < 4; r++) {
+                    const int e = threadIdx.x + r * kThr;
+                    const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
+                    sA[ki][mi] = ra[r];
+                    const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
+                    sB[kj][nj] = rb[r];
+                }
+            };
+            gload(0);
+            for (int k0 = 0; k0 < K; k0 += TK) {
+                __syncthreads();                 // previous chunk fully consumed
+                sstore();
+                __syncthreads();
+                if (k0 + TK < K) gload(k0 + TK);
 #pragma unroll
-                    for (int j = 0; j < 4; j++) best[i][j] = __viaddmax_s32(a[i], bb[j], best[i][j]);
+                for (int kk = 0; kk < TK; kk++) {
+                    const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
+                    const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                    const int a[4] = {a4.x, a4.y, a4.z, a4.w};
+                    const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++) best[i][j] = __viaddmax_s32(a[i], bb[j], best[i][j]);
+                }
             }
-            __syncthreads();
         }
 #pragma unroll
         for (int i = 0; i < 4; i++)
@@ -208,8 +234,7 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
 size_t tiled_smem(int nk, int np) {
     const size_t K = (size_t)1 << nk;
     size_t s = 2 * K * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
-    const int planes = np > 0 ? np : 1;
-    s += (size_t)planes * TK * (TM + 2) * 8 + (size_t)planes * TK * (TN + 2) * 8;
+    if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (TN + 2) * 8;   // count tiles
     return s;
 }
 
