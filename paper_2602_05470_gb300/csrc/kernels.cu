@@ -48,7 +48,13 @@ k_contract(const __grid_constant__ ContractParams P) {
     uint32_t *kB = ktab + KT;
 
     // address tables: output bits -> operand offsets (4 chunks of 8 bits)
-    for (int i = threadIdx.x; i < 1024; i += blockDim.x) {
+    // only the chunks the output rank reaches; entry 0 of the others is read as 0
+    const int nch = (P.rc + 7) >> 3;
+    if (threadIdx.x < 4 && (int)threadIdx.x >= nch) {
+        tA[threadIdx.x][0] = 0;
+        tB[threadIdx.x][0] = 0;
+    }
+    for (int i = threadIdx.x; i < (nch << 8); i += blockDim.x) {
         const int ch = i >> 8, v = i & 255;
         uint32_t a = 0, b = 0;
 #pragma unroll
