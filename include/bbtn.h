@@ -193,6 +193,12 @@ typedef struct {
     double prof_big_ms;      /* the same for launches moving >= 64 MiB */
     double prof_big_bytes;
     int64_t prof_big_launches;
+    double prof_stream_ms;   /* streaming gather kernel (K1/K3): device time, bytes, launches */
+    double prof_stream_bytes;
+    int64_t prof_stream_launches;
+    double prof_tiled_ms;    /* register-tiled kernel (K1t): device time, multiply-adds, launches */
+    double prof_tiled_ops;
+    int64_t prof_tiled_launches;
     int reserved[8];
 } bbtn_stats;
 

@@ -41,7 +41,10 @@ class Stats(C.Structure):
                 ("tc_log2", C.c_double), ("sc_plain_log2", C.c_double), ("slices_log2", C.c_int),
                 ("prof_ms", C.c_double), ("prof_bytes", C.c_double), ("prof_ops", C.c_double),
                 ("prof_launches", C.c_int64), ("prof_big_ms", C.c_double), ("prof_big_bytes", C.c_double),
-                ("prof_big_launches", C.c_int64), ("reserved", C.c_int * 8)]
+                ("prof_big_launches", C.c_int64), ("prof_stream_ms", C.c_double),
+                ("prof_stream_bytes", C.c_double), ("prof_stream_launches", C.c_int64),
+                ("prof_tiled_ms", C.c_double), ("prof_tiled_ops", C.c_double), ("prof_tiled_launches", C.c_int64),
+                ("reserved", C.c_int * 8)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}

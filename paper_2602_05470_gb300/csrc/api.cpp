@@ -138,7 +138,15 @@ int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *
         P.vc = vc;
         P.cc = cc;
         P.planeC = 1ull << rc;
-        cudaError_t e = launch_contract(P, (cudaStream_t)stream);
+        cudaStream_t s = (cudaStream_t)stream;
+        void *scratch = nullptr;
+        size_t sb = 0;
+        if (splitk_eligible(P)) {   // few outputs, long sums: split-K needs a small scratch
+            sb = splitk_scratch_bytes(rc, np);
+            BBTN_CUDA(cudaMallocAsync(&scratch, sb, s));
+        }
+        cudaError_t e = launch_contract(P, s, nullptr, scratch, sb);
+        if (scratch) cudaFreeAsync(scratch, s);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract: ") + cudaGetErrorString(e));
     });
 }

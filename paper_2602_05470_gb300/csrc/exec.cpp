@@ -120,10 +120,13 @@ void Profiler::collect() {
         float t = 0;
         BBTN_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
         ms += t;
-        if (dump) fprintf(dump, "%d,%d,%d,%d,%d,%.0f,%.0f,%.5f\n", r.ra, r.rb, r.rc, r.rs, r.ident, r.bytes, r.ops, t);
+        if (dump)
+            fprintf(dump, "%d,%d,%d,%d,%d,%.0f,%.0f,%.5f,%d\n", r.ra, r.rb, r.rc, r.rs, r.ident, r.bytes, r.ops, t, r.kind);
         bytes += r.bytes;
         ops += r.ops;
         launches++;
+        if (r.kind == 0 || r.kind == 3) { stream_ms += t; stream_bytes += r.bytes; stream_launches++; }
+        if (r.kind == 2) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
         if (r.bytes >= kBig) {
             big_ms += t;
             big_bytes += r.bytes;
@@ -274,6 +277,16 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, Fre
         }
     }
     plan.arena_bytes = fl.peak;
+    // one shared scratch region for the split-K steps (they run one after another)
+    for (int i = 0; i < nsteps; i++) {
+        const PStep &ps = plan.steps[i];
+        if (!ps.fused && splitk_eligible(ps.P))
+            plan.splitk_bytes = std::max<uint64_t>(plan.splitk_bytes, splitk_scratch_bytes(ps.P.rc, np));
+    }
+    if (plan.splitk_bytes) {
+        plan.splitk_off = align256(plan.arena_bytes);
+        plan.arena_bytes = plan.splitk_off + plan.splitk_bytes;
+    }
     // the fused program
     for (int r : roots) {
         const int last = plan.node_step[r], first = last - nint(r) + 1;
@@ -573,7 +586,9 @@ void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *
             eb = pr->get();
             BBTN_CUDA(cudaEventRecord(ea, s));
         }
-        cudaError_t e = launch_contract(P, s);
+        int kind = 0;
+        cudaError_t e = launch_contract(P, s, &kind, plan.splitk_bytes ? arena + plan.splitk_off : nullptr,
+                                        plan.splitk_bytes);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract kernel: ") + cudaGetErrorString(e));
         if (pr) {
             BBTN_CUDA(cudaEventRecord(eb, s));
@@ -581,7 +596,7 @@ void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *
             for (int i = 0; i < P.rc; i++) { if (P.oA[i] >= 0) ra++; if (P.oB[i] >= 0) rb++; }
             for (int j = 0; j < P.rs; j++) { if (P.sA[j] >= 0) ra++; if (P.sB[j] >= 0) rb++; }
             while (ident < P.rc && P.oA[ident] == ident && P.oB[ident] < 0) ident++;
-            pr->recs.push_back({ea, eb, ps.bytes, ps.ops, ra, rb, P.rc, P.rs, ident, 0});
+            pr->recs.push_back({ea, eb, ps.bytes, ps.ops, ra, rb, P.rc, P.rs, ident, kind});
         }
         if (st) st->launches++;
     }

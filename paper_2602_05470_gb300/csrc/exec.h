@@ -61,6 +61,8 @@ struct Plan {
     std::vector<FSub> fsubs;
     size_t fused_smem = 0;
     int64_t fused_steps = 0;
+    // scratch of the split-K steps (K1s), at the end of the arena
+    uint64_t splitk_off = 0, splitk_bytes = 0;
 };
 
 // Element layout of an arena block of rank r with np count planes.
@@ -83,6 +85,8 @@ struct Profiler {
     size_t used = 0;
     double ms = 0, bytes = 0, ops = 0, big_ms = 0, big_bytes = 0;
     int64_t launches = 0, big_launches = 0;
+    double stream_ms = 0, stream_bytes = 0, tiled_ms = 0, tiled_ops = 0;   // per kernel
+    int64_t stream_launches = 0, tiled_launches = 0;
     cudaEvent_t get();
     void collect();          // after the stream has been synchronised
     ~Profiler();

@@ -421,12 +421,20 @@ cudaError_t launch_contract_stream(const ContractParams &p, cudaStream_t s) {
     return p.hasB ? dispatch_contract<true>(p, s) : dispatch_contract<false>(p, s);
 }
 
-cudaError_t launch_contract(const ContractParams &p, cudaStream_t s) {
+cudaError_t launch_contract(const ContractParams &p, cudaStream_t s, int *kind, void *scratch, size_t scratch_bytes) {
     if (p.rc < 0 || p.rc > 30 || p.rs < 0 || p.rs > 40) return cudaErrorInvalidValue;
+    if (scratch && splitk_eligible(p)) {
+        if (kind) *kind = 3;
+        return launch_contract_splitk(p, scratch, scratch_bytes, s);
+    }
     if (p.hasB) {
         cudaError_t e = launch_contract_tiled(p, s);
-        if (e != cudaErrorNotSupported) return e;
+        if (e != cudaErrorNotSupported) {
+            if (kind) *kind = 2;
+            return e;
+        }
     }
+    if (kind) *kind = 0;
     return launch_contract_stream(p, s);
 }
 

@@ -205,7 +205,7 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
     rs.prof = opts_.profile ? &prof_ : nullptr;
     if (rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
         prof_.dump = fopen(getenv("BBTN_PROFILE_DUMP"), "w");
-        if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms\n");
+        if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms,kind\n");
     }
     for (int64_t i = 0; i < n; i++) {
         const double tp = now_s();
@@ -246,6 +246,12 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
         st_->prof_big_ms = prof_.big_ms;
         st_->prof_big_bytes = prof_.big_bytes;
         st_->prof_big_launches = prof_.big_launches;
+        st_->prof_stream_ms = prof_.stream_ms;
+        st_->prof_stream_bytes = prof_.stream_bytes;
+        st_->prof_stream_launches = prof_.stream_launches;
+        st_->prof_tiled_ms = prof_.tiled_ms;
+        st_->prof_tiled_ops = prof_.tiled_ops;
+        st_->prof_tiled_launches = prof_.tiled_launches;
     }
     st_->kernel_ms += ms;
     st_->t_device_s += now_s() - tw;

@@ -31,6 +31,11 @@ struct Groups {
     int8_t kA[30], kB[30];
 };
 
+// summed-label offsets: three 256-entry tables (bits 0-7, 8-15, 16-23 of k)
+__device__ __forceinline__ uint32_t kof(const uint32_t *t, uint32_t k) {
+    return t[k & 255] + t[256 + ((k >> 8) & 255)] + t[512 + ((k >> 16) & 255)];
+}
+
 __device__ __forceinline__ uint64_t deposit(uint64_t x, const int8_t *pos, int n) {
     uint64_t r = 0;
     for (int j = 0; j < n; j++)
@@ -51,7 +56,7 @@ __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const u
         int mi, ki;
         if (fast_k) { ki = e & (TK - 1); mi = e >> 4; }
         else { mi = e & (TM - 1); ki = e >> 6; }
-        const uint64_t off = base + rowoff[mi] + koff[k0 + ki];
+        const uint64_t off = base + rowoff[mi] + kof(koff, k0 + ki);
         const int32_t x = __ldg(v + off);
         if (VALS) sv[ki][mi] = x;
         if constexpr (NP > 0) {
@@ -67,11 +72,12 @@ template <int NP>
 __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1)
 k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups G, int fastA_k, int fastB_k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // layout: koffA[K], koffB[K], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4], sB[TK][TN+4], counts
+    // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
+    // sB[TK][TN+4], counts
     const int K = 1 << G.nk;
     uint32_t *koffA = (uint32_t *)smem_raw;
-    uint32_t *koffB = koffA + K;
-    uint32_t *rowA = koffB + K;
+    uint32_t *koffB = koffA + 768;
+    uint32_t *rowA = koffB + 768;
     uint32_t *colB = rowA + TM;
     uint32_t *rowC = colB + TN;
     uint32_t *colC = rowC + TM;
@@ -89,9 +95,10 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
     const uint64_t baseA = P.A.base + deposit(b, G.bA, G.nb);
     const uint64_t baseB = P.B.base + deposit(b, G.bB, G.nb);
     const uint64_t baseC = deposit(b, G.bC, G.nb);
-    for (int i = threadIdx.x; i < K; i += kThr) {
-        koffA[i] = (uint32_t)deposit(i, G.kA, G.nk);
-        koffB[i] = (uint32_t)deposit(i, G.kB, G.nk);
+    for (int i = threadIdx.x; i < 768; i += kThr) {
+        const uint64_t x = (uint64_t)(i & 255) << (8 * (i >> 8));
+        koffA[i] = (uint32_t)deposit(x, G.kA, G.nk);
+        koffB[i] = (uint32_t)deposit(x, G.kB, G.nk);
     }
     for (int i = threadIdx.x; i < TM; i += kThr) {
         const uint64_t m = (uint64_t)tm * TM + i;
@@ -122,9 +129,9 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
                 for (int r = 0; r < 4; r++) {
                     const int e = threadIdx.x + r * kThr;
                     const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
-                    ra[r] = __ldg(P.A.val + baseA + rowA[mi] + koffA[k0 + ki]);
+                    ra[r] = __ldg(P.A.val + baseA + rowA[mi] + kof(koffA, k0 + ki));
                     const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
-                    rb[r] = __ldg(P.B.val + baseB + colB[nj] + koffB[k0 + kj]);
+                    rb[r] = __ldg(P.B.val + baseB + colB[nj] + kof(koffB, k0 + kj));
                 }
             };
             auto sstore = [&]() {
@@ -233,7 +240,7 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
 
 size_t tiled_smem(int nk, int np) {
     const size_t K = (size_t)1 << nk;
-    size_t s = 2 * K * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
+    size_t s = 2 * 768 * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
     if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (TN + 2) * 8;   // count tiles
     return s;
 }
@@ -276,7 +283,7 @@ cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
         g.kB[g.nk] = p.sB[j];
         g.nk++;
     }
-    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 13) return cudaErrorNotSupported;
+    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 24) return cudaErrorNotSupported;
     // lanes along k when the operand's bit 0 is a summed label, else along m / n
     const int fa = bitA0 == 0, fb = bitB0 == 0;
     switch (p.np) {

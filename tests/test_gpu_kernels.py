@@ -255,3 +255,42 @@ def test_backward_selects_a_maximiser(P):
         for i, l in enumerate(la):
             if l in lb and l not in bits:
                 assert (ia >> i) & 1 == (ib >> lb.index(l)) & 1
+
+
+# few outputs, long sums: the split-K kernel (<= 2^12 outputs, >= 2^12 summed
+# assignments); labels: outputs 0-9, summed 100+
+SPLITK = [
+    ([0, 1] + list(range(100, 114)), list(range(100, 114)) + [16, 17, 18, 19], [0, 1, 16, 17, 18, 19]),
+    (list(range(100, 118)), list(range(117, 99, -1)), []),
+    ([0, 1, 2] + list(range(100, 116)), None, [2, 0, 1]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(SPLITK)))
+@pytest.mark.parametrize("np_", [0, 3, 4])
+def test_contract_splitk_parity(P, case, np_):
+    la, lb, lc = SPLITK[case]
+    rng = np.random.default_rng(900 + case)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), -3, 3, neg_frac=0.05)
+    A = (A[0], A[1][:np_])
+    B = None
+    if lb is not None:
+        B = _rand(rng, len(lb), max(np_, 1), -3, 3, neg_frac=0.05)
+        B = (B[0], B[1][:np_])
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, None if B is None else B[0], None if B is None else B[1], lc, primes)
+    assert np.array_equal(vc, ov)
+    assert np.array_equal(cc, oc)
+
+
+def test_contract_tiled_long_sum(P):
+    """14 summed labels: beyond a whole-K shared-memory table, still tiled."""
+    la, lb, lc = _tiled_case(6, 6, 14, 0, "k", "k", "mn")
+    rng = np.random.default_rng(1414)
+    primes = P.primes(1)
+    A = _rand(rng, len(la), 1, -3, 3, neg_frac=0.02)
+    B = _rand(rng, len(lb), 1, -3, 3, neg_frac=0.02)
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
