@@ -65,6 +65,17 @@ const char *bbtn_last_error(void);
  * check prime used by the overflow guard). */
 int bbtn_primes(int n, uint64_t *primes);
 
+/*
+ * Chinese-remainder recombination (Garner's method) of k residues res[t] mod
+ * distinct primes primes[t] (host arrays) into the unique integer in
+ * [0, prod primes) as a decimal string -- the step that turns the per-prime
+ * counts of the paper's counting algebra into the exact degeneracy. Host only.
+ * *needed receives strlen + 1; buf may be NULL to query. Residues must be below
+ * their primes.
+ */
+int bbtn_crt_decimal(int k, const uint64_t *res, const uint64_t *primes, char *buf, size_t cap,
+                     size_t *needed);
+
 /* -------------------------------------------------------- device-level operations */
 /*
  * One counting-tropical pairwise contraction (paper Eq. (2), one binary step of
@@ -281,6 +292,71 @@ typedef struct {
  * rank_a, rank_b, rank_c, summed, low_identity_bits, bytes, ops.
  */
 int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path);
+
+
+/* ------------------------------------------------------------ learned branching (GNN) */
+/*
+ * A message-passing graph network that scores the vertices of a branch-and-bound
+ * sub-problem. The paper's discussion names learned policies as the replacement for
+ * its myopic branching heuristics; this model is that idea made concrete and has
+ * no counterpart in the paper's experiments. It predicts, per free vertex, the
+ * logit of x_v = 1 in an optimal configuration. The solver uses it (opts.use_gnn
+ * with a model attached by bbtn_set_gnn, MWIS instances only) for a first
+ * incumbent and for the order in which children are visited; it never prunes, so
+ * energies and counts do not depend on it.
+ *
+ * Architecture (fp32, all kernels hand-written): input features X0 (n x 8);
+ * three layers Z_l = H_{l-1} W_l + (A H_{l-1}) U_l + b_l, H_l = relu(Z_l) with
+ * hidden width 64 and A the adjacency matrix; head s = H_3 w + c.
+ * Loss: mean over masked vertices of softplus(s) - y s. Optimiser: Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameter vector (bbtn_gnn_param_count floats): for l = 1..3 W_l (din x 64,
+ * row-major), U_l (din x 64), b_l (64), din = 8 for l = 1 else 64; then w (64), c.
+ * Feature row of vertex v: [free, fixed to 0, fixed to 1, w_v / 10,
+ * free neighbours / 8, degree / 8, neighbours fixed to 1 / 8, 1].
+ */
+typedef struct bbtn_gnn bbtn_gnn;   /* opaque; owns its device buffers */
+
+#define BBTN_GNN_FEATURES 8
+
+/* Create a model on the current device with Glorot-uniform weights from `seed`. */
+int bbtn_gnn_create(uint64_t seed, bbtn_gnn **out);
+void bbtn_gnn_destroy(bbtn_gnn *g);
+int bbtn_gnn_param_count(void);
+/* Use `stream` for the model's device work (default: the legacy stream). */
+int bbtn_gnn_set_stream(bbtn_gnn *g, void *stream);
+
+/*
+ * Host-side feature rows (n x BBTN_GNN_FEATURES floats, row-major, into out) of a
+ * graph with n vertices and m edges (host int32[2m]); w: host int32[n] vertex
+ * weights (NULL = 1); fixed: host int8[n], -1 free, 0 or 1 fixed (NULL = all free).
+ */
+int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed, float *out);
+
+/* Set the graph the next forward / train calls run on (uploads CSR lists). */
+int bbtn_gnn_set_graph(bbtn_gnn *g, int n, int m, const int32_t *edges);
+
+/* Logits of every vertex: feats host float[n*8] -> scores host float[n]. Blocking. */
+int bbtn_gnn_forward(bbtn_gnn *g, const float *feats, float *scores);
+
+/*
+ * Forward + backward of the masked loss, then one Adam step with learning rate
+ * lr (lr <= 0: gradients only, parameters unchanged). labels, mask: host
+ * float[n] (labels in {0,1}; mask 0 or 1, the mean runs over mask-1 vertices).
+ * *loss receives the loss before the step. Blocking.
+ */
+int bbtn_gnn_train_step(bbtn_gnn *g, const float *feats, const float *labels, const float *mask, float lr,
+                        float *loss);
+
+/* Copy parameters / the last gradients (host float[bbtn_gnn_param_count()]).
+ * set_params also resets the Adam moments. */
+int bbtn_gnn_get_params(bbtn_gnn *g, float *p);
+int bbtn_gnn_set_params(bbtn_gnn *g, const float *p);
+int bbtn_gnn_get_grads(bbtn_gnn *g, float *grad);
+
+/* Attach a model to a solver context (borrowed; NULL detaches). Used when
+ * opts.use_gnn is set. The model must outlive its use by bbtn_solve. */
+int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *g);
 
 #ifdef __cplusplus
 }

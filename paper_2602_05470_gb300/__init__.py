@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import (BBTNError, FINITE_MIN, MAX_PRIMES, MODE_BBTN, MODE_PLAIN, MODE_SLICED, NEG,  # noqa: F401
                    Opts, Stats, check, i32_array, u64_array)
 
-__all__ = ["primes", "contract", "permute", "aggregate", "contract_backward", "Solver", "Result",
+__all__ = ["primes", "crt", "contract", "permute", "aggregate", "contract_backward", "Solver", "Result",
            "BBTNError", "NEG", "FINITE_MIN", "MODE_PLAIN", "MODE_SLICED", "MODE_BBTN", "lib_path"]
 
 
@@ -37,6 +37,17 @@ def primes(n: int = 3):
     buf = (C.c_uint64 * max(n, 1))()
     check(lib.bbtn_primes(n, buf))
     return [int(buf[i]) for i in range(n)]
+
+
+def crt(residues, moduli) -> int:
+    """The integer in [0, prod moduli) with the given residues (host Garner recombination)."""
+    lib = _lib.load()
+    k = len(residues)
+    r, p, need = u64_array(residues), u64_array(moduli), C.c_size_t()
+    check(lib.bbtn_crt_decimal(k, r, p, None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value)
+    check(lib.bbtn_crt_decimal(k, r, p, buf, need.value, C.byref(need)))
+    return int(buf.value.decode())
 
 
 def _stream(stream):
@@ -158,6 +169,11 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def set_gnn(self, model):
+        """Attach a learned scorer (paper_2602_05470_gb300.gnn.GNN) used when use_gnn is set."""
+        check(_lib.load().bbtn_set_gnn(self._ctx, model._h if model is not None else None))
+        self._gnn = model
 
     def load(self, inst):
         """inst: object with kind ('spin'|'mwis'), n, edges, J, h2, w (e.g. synth.Instance)."""

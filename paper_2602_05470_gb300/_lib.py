@@ -62,13 +62,14 @@ class PlanInfo(C.Structure):
 _lib = None
 
 _P = C.POINTER
-_i32p, _u64p, _i64p, _i8p = _P(C.c_int32), _P(C.c_uint64), _P(C.c_int64), _P(C.c_int8)
+_i32p, _u64p, _i64p, _i8p, _f32p = _P(C.c_int32), _P(C.c_uint64), _P(C.c_int64), _P(C.c_int8), _P(C.c_float)
 _vp = C.c_void_p
 
 _SIGS = {
     "bbtn_version": ([], C.c_char_p),
     "bbtn_last_error": ([], C.c_char_p),
     "bbtn_primes": ([C.c_int, _u64p], C.c_int),
+    "bbtn_crt_decimal": ([C.c_int, _u64p, _u64p, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_contract": ([C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp,
                        C.c_int, _u64p, _vp], C.c_int),
     "bbtn_permute": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
@@ -92,6 +93,18 @@ _SIGS = {
     "bbtn_analyze": ([_vp, _P(PlanInfo), C.c_char_p], C.c_int),
     "bbtn_aggregate_noalloc": ([C.c_int64, _vp, _vp, C.c_int, _u64p, _vp, _vp, _vp], C.c_int),
     "bbtn_aggregate_noalloc_max_scratch": ([], C.c_size_t),
+    "bbtn_gnn_create": ([C.c_uint64, _P(_vp)], C.c_int),
+    "bbtn_gnn_destroy": ([_vp], None),
+    "bbtn_gnn_param_count": ([], C.c_int),
+    "bbtn_gnn_set_stream": ([_vp, _vp], C.c_int),
+    "bbtn_gnn_features": ([C.c_int, C.c_int, _i32p, _i32p, _i8p, _f32p], C.c_int),
+    "bbtn_gnn_set_graph": ([_vp, C.c_int, C.c_int, _i32p], C.c_int),
+    "bbtn_gnn_forward": ([_vp, _f32p, _f32p], C.c_int),
+    "bbtn_gnn_train_step": ([_vp, _f32p, _f32p, _f32p, C.c_float, _f32p], C.c_int),
+    "bbtn_gnn_get_params": ([_vp, _f32p], C.c_int),
+    "bbtn_gnn_set_params": ([_vp, _f32p], C.c_int),
+    "bbtn_gnn_get_grads": ([_vp, _f32p], C.c_int),
+    "bbtn_set_gnn": ([_vp, _vp], C.c_int),
 }
 
 

@@ -1,11 +1,13 @@
 // extern "C" entry points declared in include/bbtn.h.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 
 #include "../../include/bbtn.h"
 #include "common.h"
 #include "exec.h"
+#include "gnn.h"
 #include "kernels.h"
 #include "network.h"
 #include "solver.h"
@@ -23,6 +25,7 @@ struct bbtn_ctx {
     SolveOutput out;
     bbtn_stats stats;
     Arena arena;
+    GnnModel *gnn = nullptr;   // borrowed (bbtn_set_gnn)
 };
 
 namespace {
@@ -84,6 +87,25 @@ int bbtn_primes(int n, uint64_t *primes) {
         const auto &tab = prime_table();
         if (n < 0 || n > (int)tab.size() || (n > 0 && !primes)) fail(BBTN_EINVAL, "bad prime count");
         for (int i = 0; i < n; i++) primes[i] = tab[i];
+    });
+}
+
+int bbtn_crt_decimal(int k, const uint64_t *res, const uint64_t *primes, char *buf, size_t cap,
+                     size_t *needed) {
+    return guarded([&] {
+        if (k < 1 || k > 64 || !res || !primes) fail(BBTN_EINVAL, "bad residue list");
+        std::vector<uint64_t> r(res, res + k), p(primes, primes + k);
+        for (int t = 0; t < k; t++) {
+            if (!is_prime_u64(p[t])) fail(BBTN_EINVAL, "moduli must be primes");
+            if (r[t] >= p[t]) fail(BBTN_EINVAL, "residue not below its modulus");
+            for (int u = 0; u < t; u++) if (p[u] == p[t]) fail(BBTN_EINVAL, "repeated modulus");
+        }
+        std::string s = crt_decimal(r, p);
+        if (needed) *needed = s.size() + 1;
+        if (buf) {
+            if (cap < s.size() + 1) fail(BBTN_EINVAL, "buffer too small");
+            memcpy(buf, s.c_str(), s.size() + 1);
+        }
     });
 }
 
@@ -358,6 +380,7 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
         BBTN_CUDA(cudaSetDevice(ctx->device));
         Solver s(ctx->opts, ctx->stream, &ctx->arena);
+        s.set_gnn(ctx->gnn);
         ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
         ctx->solved = true;
         if (ctx->out.checked) {
@@ -429,6 +452,149 @@ int bbtn_get_stats(bbtn_ctx *ctx, bbtn_stats *st) {
     return guarded([&] {
         if (!ctx || !st) fail(BBTN_EINVAL, "bad arguments");
         *st = ctx->stats;
+    });
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ learned branching (GNN)
+
+struct bbtn_gnn {
+    std::unique_ptr<GnnModel> m;
+    cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+void edge_lists(int n, int m, const int32_t *edges, std::vector<int> &ei, std::vector<int> &ej) {
+    if (n < 0 || m < 0 || (m > 0 && !edges)) fail(BBTN_EINVAL, "bad graph");
+    ei.resize(m);
+    ej.resize(m);
+    for (int k = 0; k < m; k++) {
+        ei[k] = edges[2 * k];
+        ej[k] = edges[2 * k + 1];
+        if (ei[k] < 0 || ei[k] >= n || ej[k] < 0 || ej[k] >= n || ei[k] == ej[k])
+            fail(BBTN_EINVAL, "edge endpoint out of range or self-loop");
+    }
+}
+
+bbtn_gnn *gnn_checked(bbtn_gnn *g) {
+    if (!g || !g->m) fail(BBTN_EINVAL, "gnn is NULL");
+    return g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bbtn_gnn_create(uint64_t seed, bbtn_gnn **out) {
+    return guarded([&] {
+        if (!out) fail(BBTN_EINVAL, "out is NULL");
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            fail(BBTN_ECUDA, "no CUDA device available");
+        }
+        auto g = std::make_unique<bbtn_gnn>();
+        g->m = std::make_unique<GnnModel>(seed);
+        *out = g.release();
+    });
+}
+
+void bbtn_gnn_destroy(bbtn_gnn *g) { delete g; }
+
+int bbtn_gnn_param_count(void) { return gnn_param_count(); }
+
+int bbtn_gnn_set_stream(bbtn_gnn *g, void *stream) {
+    return guarded([&] { gnn_checked(g)->stream = (cudaStream_t)stream; });
+}
+
+int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed, float *out) {
+    return guarded([&] {
+        if (!out && n > 0) fail(BBTN_EINVAL, "out is NULL");
+        std::vector<int> ei, ej;
+        edge_lists(n, m, edges, ei, ej);
+        std::vector<int32_t> wv(n, 1);
+        std::vector<int8_t> fx(n, -1);
+        for (int v = 0; v < n; v++) {
+            if (w) wv[v] = w[v];
+            if (fixed) {
+                if (fixed[v] < -1 || fixed[v] > 1) fail(BBTN_EINVAL, "fixed values must be -1, 0 or 1");
+                fx[v] = fixed[v];
+            }
+        }
+        std::vector<float> f;
+        gnn_features(n, ei, ej, wv, fx, f);
+        if (n > 0) memcpy(out, f.data(), f.size() * sizeof(float));
+    });
+}
+
+int bbtn_gnn_set_graph(bbtn_gnn *g, int n, int m, const int32_t *edges) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (n < 1) fail(BBTN_EINVAL, "graph needs at least one vertex");
+        std::vector<int> ei, ej;
+        edge_lists(n, m, edges, ei, ej);
+        g->m->set_graph(n, ei, ej, g->stream);
+    });
+}
+
+int bbtn_gnn_forward(bbtn_gnn *g, const float *feats, float *scores) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (g->m->n < 1) fail(BBTN_ESTATE, "no graph set");
+        if (!feats || !scores) fail(BBTN_EINVAL, "feats / scores missing");
+        std::vector<float> s;
+        g->m->forward(feats, s, g->stream);
+        memcpy(scores, s.data(), s.size() * sizeof(float));
+    });
+}
+
+int bbtn_gnn_train_step(bbtn_gnn *g, const float *feats, const float *labels, const float *mask, float lr,
+                        float *loss) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (g->m->n < 1) fail(BBTN_ESTATE, "no graph set");
+        if (!feats || !labels || !mask) fail(BBTN_EINVAL, "feats / labels / mask missing");
+        const float l = g->m->train_step(feats, labels, mask, lr, g->stream);
+        if (loss) *loss = l;
+    });
+}
+
+int bbtn_gnn_get_params(bbtn_gnn *g, float *p) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (!p) fail(BBTN_EINVAL, "p is NULL");
+        std::vector<float> v;
+        g->m->get_params(v);
+        memcpy(p, v.data(), v.size() * sizeof(float));
+    });
+}
+
+int bbtn_gnn_set_params(bbtn_gnn *g, const float *p) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (!p) fail(BBTN_EINVAL, "p is NULL");
+        std::vector<float> v(p, p + gnn_param_count());
+        for (float x : v) if (!std::isfinite(x)) fail(BBTN_EINVAL, "non-finite parameter");
+        g->m->set_params(v);
+    });
+}
+
+int bbtn_gnn_get_grads(bbtn_gnn *g, float *grad) {
+    return guarded([&] {
+        gnn_checked(g);
+        if (!grad) fail(BBTN_EINVAL, "grad is NULL");
+        std::vector<float> v;
+        g->m->get_grads(v);
+        memcpy(grad, v.data(), v.size() * sizeof(float));
+    });
+}
+
+int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *g) {
+    return guarded([&] {
+        if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
+        ctx->gnn = g ? gnn_checked(g)->m.get() : nullptr;
     });
 }
 

@@ -355,11 +355,47 @@ int64_t Solver::incumbent_heuristic() {
     return best;
 }
 
+// Greedy rounding of the model's logits (largest first, keeping the set
+// independent), a few times with perturbed logits; the best set found.
+int64_t Solver::incumbent_learned() {
+    const Problem &p = *p_;
+    std::vector<float> feats;
+    gnn_features(p.n, p.ei, p.ej, p.w, fx0_, feats);
+    gnn_->set_graph(p.n, p.ei, p.ej, stream_);
+    gnn_->forward(feats.data(), logit_, stream_);
+    Rng rng(opts_.seed * 131 + 3);
+    int64_t best = INT64_MIN;
+    std::vector<int> ord(p.n);
+    std::vector<float> key(p.n);
+    for (int rep = 0; rep < 8; rep++) {
+        for (int v = 0; v < p.n; v++) key[v] = logit_[v] + (rep ? (float)(0.5 * rng.uniform()) : 0.f);
+        for (int v = 0; v < p.n; v++) ord[v] = v;
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return key[a] > key[b]; });
+        std::vector<int8_t> x = fx0_;
+        for (int v : ord) {
+            if (x[v] >= 0) continue;
+            x[v] = 1;
+            for (auto &nb : p.adj[v]) if (x[nb.first] < 0) x[nb.first] = 0;
+        }
+        best = std::max(best, objective(p, x));
+    }
+    return best;
+}
+
 void Solver::run_bbtn() {
     const Problem &p = *p_;
     const int cap = opts_.space_cap_log2;
     const int K = std::max(2, std::min(opts_.region_size, 10));
     incumbent_ = incumbent_heuristic();
+    // the learned scorer: a first incumbent and the order of the children (it never
+    // prunes, so the value and the count do not depend on it)
+    const bool learned = opts_.use_gnn && gnn_ && p.kind == kMwis && p.n > 0;
+    logit_.clear();
+    if (learned) {
+        const double tg = now_s();
+        incumbent_ = std::max(incumbent_, incumbent_learned());
+        st_->t_plan_s += now_s() - tg;
+    }
     struct BNode {
         std::vector<int8_t> fx;
         int64_t ub;
@@ -598,7 +634,26 @@ void Solver::run_bbtn() {
             if (ch.ub < incumbent_) { st_->pruned++; continue; }
             kids.push_back(std::move(ch));
         }
-        std::sort(kids.begin(), kids.end(), [](const BNode &a, const BNode &b) { return a.ub < b.ub; });
+        if (learned) {
+            // agreement of each clause with the model: sum of log P(x_v = fixed value)
+            // over the variables it fixes; the most likely child is visited first
+            std::vector<std::pair<double, size_t>> key(kids.size());
+            for (size_t c = 0; c < kids.size(); c++) {
+                double a = 0;
+                for (int v = 0; v < p.n; v++)
+                    if (nd.fx[v] < 0 && kids[c].fx[v] >= 0) {
+                        const double z = kids[c].fx[v] ? logit_[v] : -logit_[v];
+                        a -= z > 0 ? std::log1p(std::exp(-z)) : -z + std::log1p(std::exp(z));
+                    }
+                key[c] = {a, c};
+            }
+            std::stable_sort(key.begin(), key.end());
+            std::vector<BNode> sorted;
+            for (auto &k2 : key) sorted.push_back(std::move(kids[k2.second]));
+            kids.swap(sorted);
+        } else {
+            std::sort(kids.begin(), kids.end(), [](const BNode &a, const BNode &b) { return a.ub < b.ub; });
+        }
         for (auto &ch : kids) stack.push_back(std::move(ch));   // best bound popped first
     }
     if (np_ > 0) {

@@ -9,6 +9,7 @@
 
 #include "../../include/bbtn.h"
 #include "exec.h"
+#include "gnn.h"
 #include "network.h"
 #include "order.h"
 
@@ -30,6 +31,8 @@ class Solver {
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
     // host-only planning summary (bbtn_analyze)
     void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);
+    // learned branch scorer (used with opts.use_gnn on MWIS instances; borrowed)
+    void set_gnn(GnnModel *g) { gnn_ = g; }
 
   private:
     struct Leafset;
@@ -41,6 +44,7 @@ class Solver {
     void run_sliced();
     void run_bbtn();
     int64_t incumbent_heuristic();
+    int64_t incumbent_learned();
     void simplify(std::vector<int8_t> &fx) const;
     CTree order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
 
@@ -70,6 +74,8 @@ class Solver {
     SolveOutput out_;
     Profiler prof_;
     DeviceBuf prog_;                    // fused-subtree programs
+    GnnModel *gnn_ = nullptr;
+    std::vector<float> logit_;          // model logits of x_v = 1 at the root
     void ensure_buffers(int64_t n);
     void release_buffers();
 };

@@ -239,7 +239,7 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
 }
 
 size_t tiled_smem(int nk, int np) {
-    const size_t K = (size_t)1 << nk;
+    (void)nk;
     size_t s = 2 * 768 * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
     if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (TN + 2) * 8;   // count tiles
     return s;

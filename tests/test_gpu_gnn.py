@@ -1,0 +1,153 @@
+"""GNN scorer kernels (forward, backward, Adam) against the float64 oracle, and
+its use inside the branch-and-bound driver.
+
+Tolerances: the kernels compute in fp32 with sums of at most a few thousand
+terms of magnitude <= ~10; relative 2e-4 of the largest entry bounds their
+rounding error at these sizes with a wide margin.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import gnn as G
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gnn():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2602_05470_gb300 import gnn
+    return gnn
+
+
+def _close(got, want, rel=2e-4):
+    scale = max(1.0, float(np.abs(want).max()))
+    err = float(np.abs(np.asarray(got, dtype=np.float64) - want).max())
+    assert err <= rel * scale, (err, scale)
+
+
+def _case(seed, N, scale=0.1, fixed_frac=0.3):
+    inst = synth.kings_subgraph(N, 0.8, seed=seed, weights="uniform10" if seed % 2 else "unit")
+    rng = np.random.default_rng(seed)
+    fixed = np.where(rng.random(inst.n) < fixed_frac, rng.integers(0, 2, inst.n), -1)
+    p = rng.normal(0.0, scale, G.param_count()).astype(np.float32)
+    y = (rng.random(inst.n) < 0.3).astype(np.float32)
+    m = (fixed < 0).astype(np.float32)
+    return inst, fixed, p, y, m
+
+
+# sizes: a few vertices (one partial block), several blocks with a ragged tail, ~1400 vertices
+SIZES = [(0, 3), (1, 9), (2, 20), (3, 42)]
+
+
+@pytest.mark.parametrize("seed,N", SIZES)
+def test_forward_matches_oracle(gnn, seed, N):
+    inst, fixed, p, _, _ = _case(seed, N)
+    model = gnn.GNN(seed=1)
+    model.set_params(p)
+    model.set_graph(inst)
+    X = gnn.features(inst, fixed)
+    s = model.forward(X)
+    want, _ = G.forward(p, G.adjacency(inst.n, inst.edges), X.astype(np.float64))
+    _close(s, want)
+
+
+@pytest.mark.parametrize("seed,N", SIZES)
+def test_loss_and_gradient_match_oracle(gnn, seed, N):
+    inst, fixed, p, y, m = _case(seed, N)
+    model = gnn.GNN(seed=1)
+    model.set_params(p)
+    model.set_graph(inst)
+    X = gnn.features(inst, fixed)
+    A = G.adjacency(inst.n, inst.edges)
+    loss = model.train_step(X, y, m, 0.0)
+    assert abs(loss - G.loss(p, A, X, y, m)) <= 1e-4 * max(1.0, abs(loss))
+    _close(model.get_grads(), G.grad(p, A, X, y, m), rel=5e-4)
+    np.testing.assert_array_equal(model.get_params(), p)     # lr = 0 leaves them alone
+
+
+def test_adam_steps_match_oracle(gnn):
+    inst, fixed, p, y, m = _case(5, 8)
+    model = gnn.GNN(seed=1)
+    model.set_params(p)
+    model.set_graph(inst)
+    X = gnn.features(inst, fixed)
+    A = G.adjacency(inst.n, inst.edges)
+    q = p.astype(np.float64)
+    mo = np.zeros_like(q)
+    vo = np.zeros_like(q)
+    for step in (1, 2, 3):
+        g = G.grad(q, A, X, y, m)
+        q, mo, vo = G.adam(q, g, mo, vo, 1e-3, step)
+        model.train_step(X, y, m, 1e-3)
+        # Adam divides by sqrt(v): a coordinate with a tiny gradient moves by up to lr
+        # whatever its sign, so compare within a fraction of lr per step
+        _close(model.get_params(), q, rel=1e-4)
+
+
+def test_edgeless_graph_and_empty_mask(gnn):
+    inst = synth.empty_graph(5)
+    rng = np.random.default_rng(3)
+    p = rng.normal(0.0, 0.1, G.param_count()).astype(np.float32)
+    model = gnn.GNN(seed=2)
+    model.set_params(p)
+    model.set_graph(inst)
+    X = gnn.features(inst)
+    want, _ = G.forward(p, G.adjacency(5, []), X.astype(np.float64))
+    _close(model.forward(X), want)
+    z = np.zeros(5, dtype=np.float32)
+    assert model.train_step(X, z, z, 1e-2) == 0.0
+    assert not np.any(model.get_grads())
+
+
+def test_single_vertex(gnn):
+    inst = synth.empty_graph(1)
+    model = gnn.GNN(seed=3)
+    model.set_graph(inst)
+    X = gnn.features(inst)
+    want, _ = G.forward(model.get_params(), G.adjacency(1, []), X.astype(np.float64))
+    _close(model.forward(X), want)
+
+
+def _solved(P, N, seed):
+    inst = synth.kings_subgraph(N, 0.8, seed=seed)
+    s = P.Solver(space_cap_log2=30, mode=P.MODE_PLAIN, n_primes=0)
+    r = s.solve(inst, count=False, config=True)
+    return inst, r.config
+
+
+def test_training_learns_and_solver_results_do_not_change(gnn):
+    """Training lowers the held-out loss well below the best constant predictor
+    (the entropy of the label rate), and the driver returns the same optimum and
+    count with the learned scorer as without it (the scorer never prunes)."""
+    import paper_2602_05470_gb300 as P
+    rng = np.random.default_rng(0)
+    train, held = [], []
+    for i in range(24):
+        inst, x = _solved(P, 8 + i % 5, 5000 + i)
+        train.append((inst, gnn.samples(inst, x, rng, 4)))
+    for i in range(6):
+        inst, x = _solved(P, 10, 9000 + i)
+        held.append((inst, gnn.samples(inst, x, rng, 2)))
+    model = gnn.GNN(seed=11)
+    before = gnn.mean_loss(model, held)
+    gnn.train(model, train, epochs=15, lr=3e-3, rng=rng)
+    after = gnn.mean_loss(model, held)
+    rate = np.mean([y[m > 0].mean() for _, smp in held for _, y, m in smp])
+    h = -(rate * np.log(rate) + (1 - rate) * np.log(1 - rate))
+    assert after < before and after < h - 0.05, (before, after, h)
+
+    for seed in (0, 1):
+        inst = synth.kings_subgraph(14, 0.8, seed=700 + seed)
+        want = oracle.solve(inst)
+        for use in (False, True):
+            s = P.Solver(space_cap_log2=8, region_size=6, batch=4, use_gnn=use)
+            s.set_gnn(model)
+            r = s.solve(inst, count=True, config=True)
+            assert (r.alpha, r.count) == (want[0], want[1])
+            x = r.config
+            assert all(not (x[i] and x[j]) for i, j in inst.edges)
+            assert sum(x) == r.alpha

@@ -1,0 +1,153 @@
+"""Host-side checks of the C-ABI library that need no GPU.
+
+The library is built in-tree if it is missing or stale. Everything here runs
+host code only: symbol exports, the prime table, the CRT recombination, the
+planner (bbtn_analyze), argument validation, and the GNN feature rows.
+"""
+import ctypes as C
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2602_05470_gb300 import build
+    build.build()
+    import paper_2602_05470_gb300 as P
+    return P
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "bbtn.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bbtn_\w+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(P):
+    lib = C.CDLL(P.lib_path())
+    names = _declared()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_strings(P):
+    lib = P._lib.load()
+    assert b"sm_103a" in lib.bbtn_version()
+    assert lib.bbtn_primes(-1, None) == P._lib.EINVAL
+    assert lib.bbtn_last_error()
+
+
+def _is_prime(n):
+    import sympy
+    return sympy.isprime(n)
+
+
+def test_prime_table(P):
+    """2^61 - c_t with c_t ascending, all prime, and no prime 2^61 - c between them."""
+    ps = P.primes(9)
+    cs = [2**61 - p for p in ps]
+    assert cs == sorted(cs) and cs[0] == 1
+    assert all(_is_prime(p) for p in ps)
+    for c in range(1, cs[-1]):
+        if c not in cs:
+            assert not _is_prime(2**61 - c), c
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 8])
+def test_crt_roundtrip(P, k):
+    ps = P.primes(k)
+    M = 1
+    for p in ps:
+        M *= p
+    rng = random.Random(k)
+    for x in [0, 1, M - 1, M // 2] + [rng.randrange(M) for _ in range(20)]:
+        assert P.crt([x % p for p in ps], ps) == x
+
+
+def test_crt_small_moduli(P):
+    """Textbook case: x = 2 mod 3, 3 mod 5, 2 mod 7 -> 23."""
+    assert P.crt([2, 3, 2], [3, 5, 7]) == 23
+
+
+def test_crt_rejects_bad_input(P):
+    with pytest.raises(P.BBTNError):
+        P.crt([1, 2], [15, 7])       # 15 is not prime
+    with pytest.raises(P.BBTNError):
+        P.crt([7], [7])              # residue not below modulus
+    with pytest.raises(P.BBTNError):
+        P.crt([1, 1], [7, 7])        # repeated modulus
+
+
+def test_context_without_device_plans_on_host(P):
+    inst = synth.kings_subgraph(12, 0.8, seed=3)
+    s = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=30)
+    info = s.analyze(inst)
+    assert info["steps"] > 0 and info["sc_log2"] >= 1 and info["ops"] > 0
+    assert info["tc_log2"] >= info["sc_log2"]
+
+
+def test_sliced_plan_respects_cap(P, tmp_path):
+    """After dynamic slicing every tensor of a slice's plan has at most 2^cap entries."""
+    inst = synth.kings_subgraph(14, 0.8, seed=4)
+    plain = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=30).analyze(inst)
+    cap = max(4, plain["sc_log2"] - 4)
+    s = P.Solver(mode=P.MODE_SLICED, space_cap_log2=cap)
+    path = str(tmp_path / "steps.csv")
+    info = s.analyze(inst, dump_path=path)
+    assert info["slices_log2"] > 0
+    rows = [list(map(float, l.split(","))) for l in open(path).read().splitlines() if l and l[0].isdigit()]
+    assert rows and max(max(r[0], r[1], r[2]) for r in rows) <= cap
+
+
+def test_analyze_dump_lists_every_step(P, tmp_path):
+    inst = synth.square_lattice(6, seed=1)
+    s = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=30)
+    path = str(tmp_path / "steps.csv")
+    info = s.analyze(inst, dump_path=path)
+    rows = [l for l in open(path).read().splitlines() if l and l[0].isdigit()]
+    assert len(rows) == info["steps"]
+
+
+def test_invalid_instances_are_rejected(P):
+    s = P.Solver()
+    bad = synth.Instance(kind="mwis", n=3, edges=[(0, 3)], J=None, h2=None, w=[1, 1, 1], geometry=None)
+    with pytest.raises(P.BBTNError) as e:
+        s.load(bad)
+    assert e.value.code == P._lib.EINVAL
+    bad = synth.Instance(kind="mwis", n=2, edges=[(0, 1)], J=None, h2=None, w=[1, 0], geometry=None)
+    with pytest.raises(P.BBTNError):
+        s.load(bad)
+
+
+def test_solve_without_device_fails_loudly(P):
+    """No CPU fallback: on a machine without a GPU the solve reports a CUDA error."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s = P.Solver()
+    s.load(synth.path_graph(5))
+    with pytest.raises(P.BBTNError) as e:
+        s.solve()
+    assert e.value.code == P._lib.ECUDA
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gnn_features_match_oracle(P, seed):
+    from oracle import gnn as G
+    from paper_2602_05470_gb300 import gnn
+    inst = synth.kings_subgraph(9, 0.8, seed=seed, weights="uniform10" if seed else "unit")
+    rng = np.random.default_rng(seed)
+    fixed = rng.integers(-1, 2, inst.n)
+    got = gnn.features(inst, fixed)
+    want = G.features(inst.n, inst.edges, inst.w, fixed)
+    np.testing.assert_allclose(got, want, rtol=1e-7, atol=0)
+    assert gnn.GNN.param_count() == G.param_count()
