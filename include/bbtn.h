@@ -171,13 +171,16 @@ typedef struct {
     int sa_iters;            /* simulated-annealing sweeps of the order finder (default 20) */
     int region_size;         /* branching-region size |R| (default 8) */
     int batch;               /* leaves contracted per batch (default 64) */
-    int use_gnn;             /* score branches with the learned model (default 0) */
+    int use_gnn;             /* use the learned scorers attached by bbtn_set_gnn (default 0) */
     int count_check;         /* overflow guard: -1 auto, 0 off, 1 on (default -1) */
     int use_symmetry;        /* spin-flip symmetry when every field is 0 (default 1) */
     int verbose;             /* progress to stderr (default 0) */
     int profile;             /* time every contraction launch with CUDA events (default 0) */
     int max_slices_log2;     /* sliced mode: refuse more than 2^this slices (default 30) */
-    int reserved[6];
+    int branch_lookahead;    /* seed of each branching region: the variable, among the this-many
+                                carrying the most overflow, whose branching has the smallest
+                                gamma (default 1: the one carrying the most overflow) */
+    int reserved[5];
 } bbtn_opts;
 
 typedef struct {
@@ -282,13 +285,18 @@ typedef struct {
     double ops;              /* its multiply-adds */
     double bytes;            /* its algorithmic bytes */
     double arena_bytes;      /* device arena the static memory plan needs */
-    int reserved[8];
+    int64_t bb_nodes;        /* BBTN mode: nodes of the search tree, expanded on the host */
+    int64_t bb_leaves;       /* BBTN mode: its leaf sub-networks */
+    int reserved[4];
 } bbtn_plan_info;
 
 /*
  * Plan the loaded instance on the host only: contraction order (and the slicing
  * set in sliced mode), and the step list of the first slice (all sliced variables
- * 0). If dump_path is not NULL, one CSV line per step is written there:
+ * 0). In BBTN mode the whole search tree is also expanded on the host (no leaf is
+ * contracted, so only the heuristic incumbent prunes) and its size reported; with
+ * opts.use_gnn and a branch scorer attached, the scorer's forward passes run on
+ * the device. If dump_path is not NULL, one CSV line per step is written there:
  * rank_a, rank_b, rank_c, summed, low_identity_bits, bytes, ops.
  */
 int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path);
@@ -313,7 +321,14 @@ int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path);
  * Parameter vector (bbtn_gnn_param_count floats): for l = 1..3 W_l (din x 64,
  * row-major), U_l (din x 64), b_l (64), din = 8 for l = 1 else 64; then w (64), c.
  * Feature row of vertex v: [free, fixed to 0, fixed to 1, w_v / 10,
- * free neighbours / 8, degree / 8, neighbours fixed to 1 / 8, 1].
+ * free neighbours / 8, degree / 8, neighbours fixed to 1 / 8, overflow share],
+ * the overflow share being the variable's part of the Eq. (4) overflow of the
+ * sub-network relative to the largest (0 where not given).
+ *
+ * Two roles (bbtn_set_gnn): a branch scorer picks the seed of each branching
+ * region among the overflow-carrying variables (trained to imitate the lookahead
+ * of opts.branch_lookahead, rows from bbtn_branch_samples); a value model predicts
+ * an optimal configuration (first incumbent, order of children; MWIS only).
  */
 typedef struct bbtn_gnn bbtn_gnn;   /* opaque; owns its device buffers */
 
@@ -329,9 +344,11 @@ int bbtn_gnn_set_stream(bbtn_gnn *g, void *stream);
 /*
  * Host-side feature rows (n x BBTN_GNN_FEATURES floats, row-major, into out) of a
  * graph with n vertices and m edges (host int32[2m]); w: host int32[n] vertex
- * weights (NULL = 1); fixed: host int8[n], -1 free, 0 or 1 fixed (NULL = all free).
+ * weights (NULL = 1); fixed: host int8[n], -1 free, 0 or 1 fixed (NULL = all free);
+ * score: host float[n] overflow shares (NULL = 0).
  */
-int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed, float *out);
+int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed,
+                      const float *score, float *out);
 
 /* Set the graph the next forward / train calls run on (uploads CSR lists). */
 int bbtn_gnn_set_graph(bbtn_gnn *g, int n, int m, const int32_t *edges);
@@ -354,9 +371,21 @@ int bbtn_gnn_get_params(bbtn_gnn *g, float *p);
 int bbtn_gnn_set_params(bbtn_gnn *g, const float *p);
 int bbtn_gnn_get_grads(bbtn_gnn *g, float *grad);
 
-/* Attach a model to a solver context (borrowed; NULL detaches). Used when
- * opts.use_gnn is set. The model must outlive its use by bbtn_solve. */
-int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *g);
+/* Attach models to a solver context (borrowed; NULL detaches that role). Used
+ * when opts.use_gnn is set. They must outlive their use by bbtn_solve. */
+int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *branch_scorer, bbtn_gnn *value_model);
+
+/*
+ * Training rows for the branch scorer: expands the search tree of the loaded
+ * instance on the host (as bbtn_analyze in BBTN mode, seeds chosen by a lookahead
+ * over `lookahead` candidates) and records up to max_rows expanded nodes: fx
+ * (int8[max_rows*n], -1 free / 0 / 1), score (float[max_rows*n], overflow share)
+ * and gamma (float[max_rows*n]: the branching factor of the region seeded at that
+ * variable; -1 for variables that carry no overflow, 0 where the region admits no
+ * feasible configuration). *rows receives the rows written. Host only.
+ */
+int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, float *score, float *gamma,
+                        int *rows);
 
 #ifdef __cplusplus
 }

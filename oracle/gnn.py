@@ -6,8 +6,8 @@ code with the library. The paper gives no network of its own (its discussion onl
 proposes learned policies in place of the myopic branching heuristics), so the
 definition followed here is the one fixed by the library's public interface:
 
-  features of v: [free, fixed 0, fixed 1, w_v/10, free neighbours/8, degree/8,
-                  neighbours fixed to 1 / 8, 1]
+  features of v: [free, fixed 0, fixed 1, |w_v|/10, free neighbours/8, degree/8,
+                  neighbours fixed to 1 / 8, overflow share (an input, 0 if absent)]
   layer l = 1..3: Z_l = H_{l-1} W_l + A H_{l-1} U_l + b_l,  H_l = relu(Z_l),  H_0 = X
   head:           s = H_3 w + c
   loss:           sum_v m_v (softplus(s_v) - y_v s_v) / sum_v m_v
@@ -57,7 +57,7 @@ def adjacency(n, edges):
     return A
 
 
-def features(n, edges, w=None, fixed=None):
+def features(n, edges, w=None, fixed=None, score=None):
     """Feature matrix (n x 8) by its definition, vertex by vertex."""
     fx = [-1] * n if fixed is None else [int(v) for v in fixed]
     wv = [1] * n if w is None else [int(v) for v in w]
@@ -74,7 +74,7 @@ def features(n, edges, w=None, fixed=None):
         X[v, 4] = sum(1 for u in nbr[v] if fx[u] == -1) / 8.0
         X[v, 5] = len(nbr[v]) / 8.0
         X[v, 6] = sum(1 for u in nbr[v] if fx[u] == 1) / 8.0
-        X[v, 7] = 1.0
+        X[v, 7] = 0.0 if score is None else float(score[v])
     return X
 
 

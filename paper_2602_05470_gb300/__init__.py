@@ -143,14 +143,14 @@ class Solver:
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
-                 profile: bool = False, stream=None, workspace=None):
+                 profile: bool = False, branch_lookahead: int = 1, stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
         o.mode, o.space_cap_log2, o.n_primes, o.seed = mode, space_cap_log2, n_primes, seed
         o.sa_iters, o.region_size, o.batch, o.use_gnn = sa_iters, region_size, batch, int(use_gnn)
         o.count_check, o.use_symmetry = count_check, int(use_symmetry)
-        o.max_slices_log2, o.profile = max_slices_log2, int(profile)
+        o.max_slices_log2, o.profile, o.branch_lookahead = max_slices_log2, int(profile), branch_lookahead
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:
@@ -170,10 +170,27 @@ class Solver:
         except Exception:
             pass
 
-    def set_gnn(self, model):
-        """Attach a learned scorer (paper_2602_05470_gb300.gnn.GNN) used when use_gnn is set."""
-        check(_lib.load().bbtn_set_gnn(self._ctx, model._h if model is not None else None))
-        self._gnn = model
+    def set_gnn(self, branch=None, value=None):
+        """Attach learned scorers (paper_2602_05470_gb300.gnn.GNN), used when use_gnn is set:
+        `branch` picks the seed of each branching region, `value` predicts an optimum."""
+        check(_lib.load().bbtn_set_gnn(self._ctx, branch._h if branch is not None else None,
+                                       value._h if value is not None else None))
+        self._gnn = (branch, value)
+
+    def branch_samples(self, inst, max_rows: int, lookahead: int):
+        """Host-side search rows for the branch scorer: (fx, score, gamma), each max_rows' x n."""
+        import numpy as np
+        self.load(inst)
+        n = inst.n
+        fx = np.zeros((max_rows, n), dtype=np.int8)
+        sc = np.zeros((max_rows, n), dtype=np.float32)
+        ga = np.zeros((max_rows, n), dtype=np.float32)
+        rows = C.c_int()
+        f32 = C.POINTER(C.c_float)
+        check(_lib.load().bbtn_branch_samples(self._ctx, max_rows, lookahead, fx.ctypes.data_as(_lib._i8p),
+                                              sc.ctypes.data_as(f32), ga.ctypes.data_as(f32), C.byref(rows)))
+        r = rows.value
+        return fx[:r], sc[:r], ga[:r]
 
     def load(self, inst):
         """inst: object with kind ('spin'|'mwis'), n, edges, J, h2, w (e.g. synth.Instance)."""

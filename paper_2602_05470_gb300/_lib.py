@@ -30,7 +30,7 @@ class Opts(C.Structure):
                 ("mode", C.c_int), ("sa_iters", C.c_int), ("region_size", C.c_int),
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
-                ("max_slices_log2", C.c_int), ("reserved", C.c_int * 6)]
+                ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class Stats(C.Structure):
@@ -53,7 +53,8 @@ class Stats(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("tc_log2", C.c_double), ("sc_log2", C.c_int), ("rho", C.c_double),
                 ("slices_log2", C.c_int), ("steps", C.c_int64), ("ops", C.c_double), ("bytes", C.c_double),
-                ("arena_bytes", C.c_double), ("reserved", C.c_int * 8)]
+                ("arena_bytes", C.c_double), ("bb_nodes", C.c_int64), ("bb_leaves", C.c_int64),
+                ("reserved", C.c_int * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -97,14 +98,15 @@ _SIGS = {
     "bbtn_gnn_destroy": ([_vp], None),
     "bbtn_gnn_param_count": ([], C.c_int),
     "bbtn_gnn_set_stream": ([_vp, _vp], C.c_int),
-    "bbtn_gnn_features": ([C.c_int, C.c_int, _i32p, _i32p, _i8p, _f32p], C.c_int),
+    "bbtn_gnn_features": ([C.c_int, C.c_int, _i32p, _i32p, _i8p, _f32p, _f32p], C.c_int),
     "bbtn_gnn_set_graph": ([_vp, C.c_int, C.c_int, _i32p], C.c_int),
     "bbtn_gnn_forward": ([_vp, _f32p, _f32p], C.c_int),
     "bbtn_gnn_train_step": ([_vp, _f32p, _f32p, _f32p, C.c_float, _f32p], C.c_int),
     "bbtn_gnn_get_params": ([_vp, _f32p], C.c_int),
     "bbtn_gnn_set_params": ([_vp, _f32p], C.c_int),
     "bbtn_gnn_get_grads": ([_vp, _f32p], C.c_int),
-    "bbtn_set_gnn": ([_vp, _vp], C.c_int),
+    "bbtn_set_gnn": ([_vp, _vp, _vp], C.c_int),
+    "bbtn_branch_samples": ([_vp, C.c_int, C.c_int, _i8p, _f32p, _f32p, _P(C.c_int)], C.c_int),
 }
 
 

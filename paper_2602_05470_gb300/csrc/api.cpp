@@ -25,7 +25,8 @@ struct bbtn_ctx {
     SolveOutput out;
     bbtn_stats stats;
     Arena arena;
-    GnnModel *gnn = nullptr;   // borrowed (bbtn_set_gnn)
+    GnnModel *gnn_branch = nullptr;   // borrowed (bbtn_set_gnn)
+    GnnModel *gnn_value = nullptr;
 };
 
 namespace {
@@ -263,6 +264,7 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->verbose = 0;
     o->profile = 0;
     o->max_slices_log2 = 30;
+    o->branch_lookahead = 1;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -278,6 +280,7 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
         if (o.region_size < 1 || o.region_size > 16) fail(BBTN_EINVAL, "region_size outside 1..16");
         if (o.batch < 1) fail(BBTN_EINVAL, "batch < 1");
         if (o.sa_iters < 0) fail(BBTN_EINVAL, "sa_iters < 0");
+        if (o.branch_lookahead < 0 || o.branch_lookahead > 1024) fail(BBTN_EINVAL, "branch_lookahead outside 0..1024");
         // without a usable device the context still plans on the host (bbtn_analyze);
         // every call that needs the device then fails with BBTN_ECUDA
         if (cudaGetDevice(&ctx->device) == cudaSuccess &&
@@ -380,7 +383,7 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
         BBTN_CUDA(cudaSetDevice(ctx->device));
         Solver s(ctx->opts, ctx->stream, &ctx->arena);
-        s.set_gnn(ctx->gnn);
+        s.set_gnn(ctx->gnn_branch, ctx->gnn_value);
         ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
         ctx->solved = true;
         if (ctx->out.checked) {
@@ -444,6 +447,7 @@ int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path) {
         if (!ctx || !info) fail(BBTN_EINVAL, "bad arguments");
         if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
         Solver s(ctx->opts, ctx->stream, &ctx->arena);
+        s.set_gnn(ctx->gnn_branch, nullptr);   // a branch scorer runs on the device
         s.analyze(ctx->prob, info, dump_path);
     });
 }
@@ -509,7 +513,8 @@ int bbtn_gnn_set_stream(bbtn_gnn *g, void *stream) {
     return guarded([&] { gnn_checked(g)->stream = (cudaStream_t)stream; });
 }
 
-int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed, float *out) {
+int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, const int8_t *fixed,
+                      const float *score, float *out) {
     return guarded([&] {
         if (!out && n > 0) fail(BBTN_EINVAL, "out is NULL");
         std::vector<int> ei, ej;
@@ -523,8 +528,9 @@ int bbtn_gnn_features(int n, int m, const int32_t *edges, const int32_t *w, cons
                 fx[v] = fixed[v];
             }
         }
-        std::vector<float> f;
-        gnn_features(n, ei, ej, wv, fx, f);
+        std::vector<float> f, sc;
+        if (score) sc.assign(score, score + n);
+        gnn_features(n, ei, ej, wv, fx, f, score ? &sc : nullptr);
         if (n > 0) memcpy(out, f.data(), f.size() * sizeof(float));
     });
 }
@@ -591,10 +597,39 @@ int bbtn_gnn_get_grads(bbtn_gnn *g, float *grad) {
     });
 }
 
-int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *g) {
+int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *branch_scorer, bbtn_gnn *value_model) {
     return guarded([&] {
         if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
-        ctx->gnn = g ? gnn_checked(g)->m.get() : nullptr;
+        ctx->gnn_branch = branch_scorer ? gnn_checked(branch_scorer)->m.get() : nullptr;
+        ctx->gnn_value = value_model ? gnn_checked(value_model)->m.get() : nullptr;
+    });
+}
+
+int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, float *score, float *gamma,
+                        int *rows) {
+    return guarded([&] {
+        if (!ctx || !rows) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        if (max_rows < 0 || (max_rows > 0 && (!fx || !score || !gamma))) fail(BBTN_EINVAL, "bad row buffers");
+        const int n = ctx->prob.n;
+        BranchLog log;
+        log.max = max_rows;
+        log.lookahead = std::max(1, lookahead);
+        log.fx.assign((size_t)max_rows * n, -1);
+        log.score.assign((size_t)max_rows * n, 0.f);
+        log.gamma.assign((size_t)max_rows * n, -1.f);
+        bbtn_opts o = ctx->opts;
+        o.mode = BBTN_MODE_BBTN;
+        Solver s(o, nullptr, &ctx->arena);
+        bbtn_stats st;
+        s.branch_samples(ctx->prob, &log, &st);
+        const size_t cnt = (size_t)log.count * n;
+        if (cnt) {
+            memcpy(fx, log.fx.data(), cnt);
+            memcpy(score, log.score.data(), cnt * sizeof(float));
+            memcpy(gamma, log.gamma.data(), cnt * sizeof(float));
+        }
+        *rows = log.count;
     });
 }
 

@@ -11,6 +11,7 @@ namespace bbtn {
 constexpr int kGnnFeat = 8;     // input features per vertex
 constexpr int kGnnHidden = 64;  // hidden width
 constexpr int kGnnLayers = 3;
+constexpr int kGnnBranchCandidates = 16;   // seeds a branch scorer chooses among (at least)
 
 cudaError_t gnn_gather(int n, int d, const int *rowp, const int *col, const float *H, float *M, cudaStream_t s);
 cudaError_t gnn_dense(int n, int din, int dout, const float *X, const float *M, const float *W, const float *U,
@@ -32,9 +33,10 @@ cudaError_t gnn_adam(int np, float *p, const float *g, float *m, float *v, float
 int gnn_param_count();
 
 // Per-vertex input features of a sub-problem: fx[v] = -1 free, 0 / 1 fixed; w:
-// vertex weights (MWIS) or |field| (spin glass). Row-major n x kGnnFeat.
+// vertex weights (MWIS) or |2 h_v| (spin glass); score: the variable's share of the
+// overflow (0..1; NULL = 0). Row-major n x kGnnFeat.
 void gnn_features(int n, const std::vector<int> &ei, const std::vector<int> &ej, const std::vector<int32_t> &w,
-                  const std::vector<int8_t> &fx, std::vector<float> &out);
+                  const std::vector<int8_t> &fx, std::vector<float> &out, const std::vector<float> *score = nullptr);
 
 class GnnModel {
   public:

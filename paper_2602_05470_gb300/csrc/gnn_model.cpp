@@ -44,7 +44,7 @@ const Layout &layout() {
 int gnn_param_count() { return layout().total; }
 
 void gnn_features(int n, const std::vector<int> &ei, const std::vector<int> &ej, const std::vector<int32_t> &w,
-                  const std::vector<int8_t> &fx, std::vector<float> &out) {
+                  const std::vector<int8_t> &fx, std::vector<float> &out, const std::vector<float> *score) {
     out.assign((size_t)n * kGnnFeat, 0.f);
     std::vector<int> deg(n, 0), fdeg(n, 0), ones(n, 0);
     for (size_t k = 0; k < ei.size(); k++) {
@@ -65,7 +65,7 @@ void gnn_features(int n, const std::vector<int> &ei, const std::vector<int> &ej,
         f[4] = fdeg[v] / 8.f;
         f[5] = deg[v] / 8.f;
         f[6] = ones[v] / 8.f;
-        f[7] = 1.f;
+        f[7] = score ? (*score)[v] : 0.f;
     }
 }
 

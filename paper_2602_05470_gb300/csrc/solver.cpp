@@ -51,6 +51,227 @@ Overflow overflow_of(const CTree &t, const std::vector<int8_t> &fx, int cap) {
     return o;
 }
 
+// One branching step at a node (paper: branching region R, feasible local
+// configurations F(R), optimal branching D(R)). R is grown from `seed` by BFS over
+// free variables, preferring overflow-carrying ones. Returns gamma of the chosen
+// D(R) (0 when F(R) is empty: the node holds no feasible configuration) and the
+// clauses as base-3 states over R (digit 0 free, 1 fixed to 0, 2 fixed to 1).
+double branch_at(const Problem &p, const CTree &tree, int cap, const std::vector<int8_t> &fx, const Overflow &ov,
+                 const std::vector<double> &score, int seed, int K, std::vector<int> &R,
+                 std::vector<int> &clause_states) {
+    std::vector<int> pow3(K + 1, 1);
+    for (int i = 1; i <= K; i++) pow3[i] = pow3[i - 1] * 3;
+    R.clear();
+    clause_states.clear();
+    const auto &tree_ = tree;
+    R.push_back(seed);
+    std::vector<char> inR(p.n, 0);
+    inR[seed] = 1;
+    while ((int)R.size() < K) {
+        int pick = -1;
+        double pk = -1;
+        for (int v : R)
+            for (auto &nb : p.adj[v]) {
+                int u = nb.first;
+                if (inR[u] || fx[u] >= 0) continue;
+                int links = 0;
+                for (auto &nb2 : p.adj[u]) if (inR[nb2.first]) links++;
+                double key = score[u] + 0.25 * links;
+                if (key > pk) { pk = key; pick = u; }
+            }
+        if (pick < 0) break;
+        R.push_back(pick);
+        inR[pick] = 1;
+    }
+    const int k = (int)R.size();
+    // ---- feasible local configurations F(R): boundary equivalence (per boundary
+    // state keep every configuration of maximal local value -- ties kept)
+    std::vector<int> bpos;    // indices into R of boundary variables
+    for (int i = 0; i < k; i++) {
+        bool b = false;
+        for (auto &nb : p.adj[R[i]]) if (!inR[nb.first] && fx[nb.first] < 0) { b = true; break; }
+        if (b) bpos.push_back(i);
+    }
+    std::vector<int64_t> lval(1u << k);
+    std::vector<char> feas(1u << k, 1);
+    for (uint32_t c = 0; c < (1u << k); c++) {
+        int64_t val = 0;
+        for (int i = 0; i < k && feas[c]; i++) {
+            const int v = R[i];
+            const int xi = (c >> i) & 1;
+            if (p.kind == kMwis) {
+                if (xi) {
+                    val += p.w[v];
+                    for (auto &nb : p.adj[v]) {
+                        int u = nb.first;
+                        if (fx[u] == 1) { feas[c] = 0; break; }
+                        if (inR[u]) {
+                            int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
+                            if ((c >> j) & 1) { feas[c] = 0; break; }
+                        }
+                    }
+                }
+            } else {
+                int64_t eff = p.h2[v];
+                for (auto &nb : p.adj[v]) {
+                    int u = nb.first;
+                    if (fx[u] >= 0) eff += 2ll * p.J[nb.second] * (2 * fx[u] - 1);
+                    else if (inR[u] && u > v) {
+                        int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
+                        val += 2ll * p.J[nb.second] * (2 * xi - 1) * (2 * ((c >> j) & 1) - 1);
+                    }
+                }
+                val += eff * (2 * xi - 1);
+            }
+        }
+        lval[c] = val;
+    }
+    const int nb = (int)bpos.size();
+    std::vector<int64_t> bestb(1u << nb, INT64_MIN);
+    auto bstate = [&](uint32_t c) {
+        uint32_t b = 0;
+        for (int q = 0; q < nb; q++) b |= ((c >> bpos[q]) & 1u) << q;
+        return b;
+    };
+    for (uint32_t c = 0; c < (1u << k); c++)
+        if (feas[c]) bestb[bstate(c)] = std::max(bestb[bstate(c)], lval[c]);
+    if (p.kind == kMwis) {
+        // fewer boundary members never constrain the outside more: a strictly
+        // better configuration on a subset of the boundary dominates
+        for (int q = 0; q < nb; q++)
+            for (uint32_t b = 0; b < (1u << nb); b++)
+                if ((b >> q) & 1) bestb[b] = std::max(bestb[b], bestb[b ^ (1u << q)]);
+    }
+    std::vector<uint32_t> F;
+    for (uint32_t c = 0; c < (1u << k); c++)
+        if (feas[c] && lval[c] == bestb[bstate(c)]) F.push_back(c);
+    if (F.empty()) return 0.0;
+    // ---- optimal branching D(R): a decision tree over R whose leaves (clauses)
+    // are complete and orthogonal by construction; minimise gamma of
+    // gamma^rho = sum_i gamma^rho_i (Eq. (4) and the characteristic equation)
+    std::vector<uint64_t> nmask(ov.nodes.size(), 0);   // R-bits carried by each overflow node
+    std::vector<int> idxR(p.n, -1);
+    for (int i = 0; i < k; i++) idxR[R[i]] = i;
+    // MWIS: a 1 in R also fixes its free neighbours (outside R too): universe U
+    std::vector<int> U(R.begin(), R.end());
+    std::vector<int> idxU(p.n, -1);
+    for (int i = 0; i < k; i++) idxU[R[i]] = i;
+    std::vector<uint64_t> nbmask(k, 0);
+    if (p.kind == kMwis) {
+        for (int i = 0; i < k; i++)
+            for (auto &nbp : p.adj[R[i]]) {
+                int u = nbp.first;
+                if (fx[u] >= 0) continue;
+                if (idxU[u] < 0 && (int)U.size() < 64) { idxU[u] = (int)U.size(); U.push_back(u); }
+                if (idxU[u] >= 0) nbmask[i] |= 1ull << idxU[u];
+            }
+    }
+    for (size_t q = 0; q < ov.nodes.size(); q++)
+        for (int l : tree_.nodes[ov.nodes[q]].lab)
+            if (idxU[l] >= 0 && fx[l] < 0) nmask[q] |= 1ull << idxU[l];
+    // overflowing tensors grouped by (R-mask, size): most carry none of U
+    double rho_const = 0;
+    std::vector<std::pair<std::pair<uint64_t, int>, int>> groups;   // ((mask, size), multiplicity)
+    {
+        std::vector<std::pair<uint64_t, int>> ms;
+        for (size_t q = 0; q < ov.nodes.size(); q++) {
+            if (nmask[q] == 0) rho_const += ov.size[q] - cap;
+            else ms.push_back({nmask[q], ov.size[q]});
+        }
+        std::sort(ms.begin(), ms.end());
+        for (auto &e : ms) {
+            if (!groups.empty() && groups.back().first == e) groups.back().second++;
+            else groups.push_back({e, 1});
+        }
+    }
+    const int S = pow3[k];
+    std::vector<double> rho(S);
+    std::vector<char> cons(S);
+    for (int s = 0; s < S; s++) {
+        uint64_t fixedm = 0;
+        int x = s;
+        for (int i = 0; i < k; i++, x /= 3) {
+            int d = x % 3;
+            if (d) {
+                fixedm |= 1ull << i;
+                if (d == 2) fixedm |= nbmask[i];
+            }
+        }
+        double r = rho_const;
+        for (auto &g : groups) {
+            const int sz = g.first.second - __builtin_popcountll(g.first.first & fixedm);
+            if (sz > cap) r += (double)(sz - cap) * g.second;
+        }
+        rho[s] = r;
+    }
+    // consistent states: some configuration of F(R) agrees with every fixed digit;
+    // each c in F marks the 2^k states that fix a subset of R to c's values
+    {
+        std::vector<int> st(1u << k);
+        for (uint32_t c : F) {
+            st[0] = 0;
+            cons[0] = 1;
+            for (uint32_t m = 1; m < (1u << k); m++) {
+                const int i = __builtin_ctz(m);
+                st[m] = st[m & (m - 1)] + (int)(((c >> i) & 1) + 1) * pow3[i];
+                cons[st[m]] = 1;
+            }
+        }
+    }
+    const double rho0 = rho[0];
+    std::vector<double> memo(S);
+    std::vector<int> choice(S);
+    // consistent states, most fixed variables first (children before parents)
+    static thread_local std::vector<std::vector<int>> by_fixed_k(11);
+    std::vector<int> &all = by_fixed_k[k];
+    if (all.empty()) {
+        std::vector<int> nfix(S);
+        for (int s = 0; s < S; s++) {
+            int x = s, nf = 0;
+            for (int i = 0; i < k; i++, x /= 3) if (x % 3) nf++;
+            nfix[s] = nf;
+            all.push_back(s);
+        }
+        std::stable_sort(all.begin(), all.end(), [&](int a, int b) { return nfix[a] > nfix[b]; });
+    }
+    std::vector<int> by_fixed;
+    by_fixed.reserve(S);
+    for (int s : all) {
+        if (cons[s]) by_fixed.push_back(s);
+        else { memo[s] = 0; choice[s] = -1; }
+    }
+    auto dp = [&](double gamma) {
+        const double lg = std::log(gamma);
+        for (int s : by_fixed) {
+            double best = s == 0 ? INFINITY : std::exp((rho[s] - rho0) * lg);
+            int bc = -1;
+            int x = s;
+            for (int i = 0; i < k; i++, x /= 3) {
+                if (x % 3) continue;
+                double c = memo[s + pow3[i]] + memo[s + 2 * pow3[i]];
+                if (c < best) { best = c; bc = i; }
+            }
+            memo[s] = best;
+            choice[s] = bc;
+        }
+        return memo[0];
+    };
+    double lo = 1.0, hi = std::ldexp(1.0, k) + 1;
+    for (int it = 0; it < 30; it++) {     // geometric bisection: ln(hi/lo) shrinks to ~5e-9
+        double mid = std::sqrt(lo * hi);
+        if (dp(mid) <= 1.0) hi = mid; else lo = mid;
+    }
+    dp(hi);
+    std::function<void(int)> collect = [&](int s) {
+        if (!cons[s]) return;
+        if (choice[s] < 0) { clause_states.push_back(s); return; }
+        collect(s + pow3[choice[s]]);
+        collect(s + 2 * pow3[choice[s]]);
+    };
+    collect(0);
+    return hi;
+}
+
 }  // namespace
 
 void Solver::ensure_buffers(int64_t n) {
@@ -382,20 +603,30 @@ int64_t Solver::incumbent_learned() {
     return best;
 }
 
-void Solver::run_bbtn() {
+void Solver::run_bbtn() { search(false, nullptr); }
+
+// The branch-and-bound search over sub-networks. Nodes are expanded depth-first
+// (best child last on the stack); a node whose reference-tree overflow is zero is a
+// leaf. dry: expand the tree on the host only (leaves are counted, not contracted;
+// the incumbent is the heuristic one). log: record, for every expanded node, its
+// fixings, the overflow score of each variable and the gamma of the branching
+// seeded at each candidate variable (the lookahead labels of the learned scorer).
+void Solver::search(bool dry, BranchLog *log) {
     const Problem &p = *p_;
     const int cap = opts_.space_cap_log2;
     const int K = std::max(2, std::min(opts_.region_size, 10));
     incumbent_ = incumbent_heuristic();
-    // the learned scorer: a first incumbent and the order of the children (it never
-    // prunes, so the value and the count do not depend on it)
-    const bool learned = opts_.use_gnn && gnn_ && p.kind == kMwis && p.n > 0;
+    // the learned scorers never prune, so the value and the count do not depend on them
+    const bool learned = !dry && opts_.use_gnn && gnn_ && p.kind == kMwis && p.n > 0;
+    const bool learned_branch = opts_.use_gnn && gnn_branch_ && p.n > 0 && !log;
     logit_.clear();
     if (learned) {
         const double tg = now_s();
         incumbent_ = std::max(incumbent_, incumbent_learned());
         st_->t_plan_s += now_s() - tg;
     }
+    if (learned_branch) gnn_branch_->set_graph(p.n, p.ei, p.ej, stream_);
+    const int lookahead = log ? std::max(1, log->lookahead) : std::max(1, opts_.branch_lookahead);
     struct BNode {
         std::vector<int8_t> fx;
         int64_t ub;
@@ -405,8 +636,10 @@ void Solver::run_bbtn() {
     std::vector<std::vector<int8_t>> batch;
     const int bs = std::max(1, opts_.batch);
     std::vector<double> score(p.n);
-    std::vector<int> pow3(K + 1, 1);
-    for (int i = 1; i <= K; i++) pow3[i] = pow3[i - 1] * 3;
+    std::vector<float> feats, blogit;
+    std::vector<int32_t> wv = p.kind == kMwis ? p.w : std::vector<int32_t>(p.n, 0);
+    if (p.kind != kMwis)
+        for (int v = 0; v < p.n; v++) wv[v] = std::abs(p.h2[v]);
 
     // Two phases: every leaf is first contracted value-only (its maximum, which also
     // raises the incumbent); only the leaves whose maximum equals the global optimum
@@ -415,6 +648,11 @@ void Solver::run_bbtn() {
     std::vector<int32_t> cand_val;
     while (!stack.empty() || !batch.empty()) {
         if (stack.empty() || (int)batch.size() >= bs) {
+            if (dry) {
+                st_->leaves += (int64_t)batch.size();
+                batch.clear();
+                continue;
+            }
             std::vector<int32_t> v = contract_leaves(batch, np_ == 0);
             if (np_ > 0) {
                 for (size_t i = 0; i < batch.size(); i++)
@@ -437,190 +675,59 @@ void Solver::run_bbtn() {
             st_->t_plan_s += now_s() - tp;
             continue;
         }
-        // ---- branching region R: seed = variable carried by the most overflow
+        // ---- seed of the branching region: by default the variable carried by the
+        // most overflow; with a lookahead the one (among the top candidates) whose
+        // branching has the smallest gamma; with the learned scorer its top pick
         std::fill(score.begin(), score.end(), 0.0);
         for (size_t q = 0; q < ov.nodes.size(); q++)
             for (int l : tree_.nodes[ov.nodes[q]].lab)
                 if (nd.fx[l] < 0) score[l] += ov.size[q] - cap;
-        int seed = -1;
+        std::vector<int> cands;
         for (int v = 0; v < p.n; v++)
-            if (nd.fx[v] < 0 && score[v] > 0 && (seed < 0 || score[v] > score[seed])) seed = v;
-        if (seed < 0) fail(BBTN_ESTATE, "no branching variable");
-        std::vector<int> R{seed};
-        std::vector<char> inR(p.n, 0);
-        inR[seed] = 1;
-        while ((int)R.size() < K) {
-            int pick = -1;
-            double pk = -1;
-            for (int v : R)
-                for (auto &nb : p.adj[v]) {
-                    int u = nb.first;
-                    if (inR[u] || nd.fx[u] >= 0) continue;
-                    int links = 0;
-                    for (auto &nb2 : p.adj[u]) if (inR[nb2.first]) links++;
-                    double key = score[u] + 0.25 * links;
-                    if (key > pk) { pk = key; pick = u; }
-                }
-            if (pick < 0) break;
-            R.push_back(pick);
-            inR[pick] = 1;
-        }
-        const int k = (int)R.size();
-        // ---- feasible local configurations F(R): boundary equivalence (per boundary
-        // state keep every configuration of maximal local value -- ties kept)
-        std::vector<int> bpos;    // indices into R of boundary variables
-        for (int i = 0; i < k; i++) {
-            bool b = false;
-            for (auto &nb : p.adj[R[i]]) if (!inR[nb.first] && nd.fx[nb.first] < 0) { b = true; break; }
-            if (b) bpos.push_back(i);
-        }
-        std::vector<int64_t> lval(1u << k);
-        std::vector<char> feas(1u << k, 1);
-        for (uint32_t c = 0; c < (1u << k); c++) {
-            int64_t val = 0;
-            for (int i = 0; i < k && feas[c]; i++) {
-                const int v = R[i];
-                const int xi = (c >> i) & 1;
-                if (p.kind == kMwis) {
-                    if (xi) {
-                        val += p.w[v];
-                        for (auto &nb : p.adj[v]) {
-                            int u = nb.first;
-                            if (nd.fx[u] == 1) { feas[c] = 0; break; }
-                            if (inR[u]) {
-                                int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
-                                if ((c >> j) & 1) { feas[c] = 0; break; }
-                            }
-                        }
-                    }
-                } else {
-                    int64_t eff = p.h2[v];
-                    for (auto &nb : p.adj[v]) {
-                        int u = nb.first;
-                        if (nd.fx[u] >= 0) eff += 2ll * p.J[nb.second] * (2 * nd.fx[u] - 1);
-                        else if (inR[u] && u > v) {
-                            int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
-                            val += 2ll * p.J[nb.second] * (2 * xi - 1) * (2 * ((c >> j) & 1) - 1);
-                        }
-                    }
-                    val += eff * (2 * xi - 1);
-                }
+            if (nd.fx[v] < 0 && score[v] > 0) cands.push_back(v);
+        if (cands.empty()) fail(BBTN_ESTATE, "no branching variable");
+        std::stable_sort(cands.begin(), cands.end(), [&](int a, int b) { return score[a] > score[b]; });
+        std::vector<int> R, clause_states;
+        double gamma = 0;
+        int seed = cands[0];
+        if (log && log->count < log->max) {
+            // the top candidates with their gamma (the labels); the search follows the lookahead
+            const size_t base = (size_t)log->count * p.n;
+            double smax = score[cands[0]];
+            double gbest = INFINITY;
+            for (int v = 0; v < p.n; v++) {
+                log->fx[base + v] = nd.fx[v];
+                log->score[base + v] = (float)(score[v] / smax);
+                log->gamma[base + v] = -1.f;
             }
-            lval[c] = val;
-        }
-        const int nb = (int)bpos.size();
-        std::vector<int64_t> bestb(1u << nb, INT64_MIN);
-        auto bstate = [&](uint32_t c) {
-            uint32_t b = 0;
-            for (int q = 0; q < nb; q++) b |= ((c >> bpos[q]) & 1u) << q;
-            return b;
-        };
-        for (uint32_t c = 0; c < (1u << k); c++)
-            if (feas[c]) bestb[bstate(c)] = std::max(bestb[bstate(c)], lval[c]);
-        if (p.kind == kMwis) {
-            // fewer boundary members never constrain the outside more: a strictly
-            // better configuration on a subset of the boundary dominates
-            for (int q = 0; q < nb; q++)
-                for (uint32_t b = 0; b < (1u << nb); b++)
-                    if ((b >> q) & 1) bestb[b] = std::max(bestb[b], bestb[b ^ (1u << q)]);
-        }
-        std::vector<uint32_t> F;
-        for (uint32_t c = 0; c < (1u << k); c++)
-            if (feas[c] && lval[c] == bestb[bstate(c)]) F.push_back(c);
-        if (F.empty()) { st_->pruned++; st_->t_plan_s += now_s() - tp; continue; }
-        // ---- optimal branching D(R): a decision tree over R whose leaves (clauses)
-        // are complete and orthogonal by construction; minimise gamma of
-        // gamma^rho = sum_i gamma^rho_i (Eq. (4) and the characteristic equation)
-        std::vector<uint64_t> nmask(ov.nodes.size(), 0);   // R-bits carried by each overflow node
-        std::vector<int> idxR(p.n, -1);
-        for (int i = 0; i < k; i++) idxR[R[i]] = i;
-        // MWIS: a 1 in R also fixes its free neighbours (outside R too): universe U
-        std::vector<int> U(R.begin(), R.end());
-        std::vector<int> idxU(p.n, -1);
-        for (int i = 0; i < k; i++) idxU[R[i]] = i;
-        std::vector<uint64_t> nbmask(k, 0);
-        if (p.kind == kMwis) {
-            for (int i = 0; i < k; i++)
-                for (auto &nbp : p.adj[R[i]]) {
-                    int u = nbp.first;
-                    if (nd.fx[u] >= 0) continue;
-                    if (idxU[u] < 0 && (int)U.size() < 64) { idxU[u] = (int)U.size(); U.push_back(u); }
-                    if (idxU[u] >= 0) nbmask[i] |= 1ull << idxU[u];
-                }
-        }
-        for (size_t q = 0; q < ov.nodes.size(); q++)
-            for (int l : tree_.nodes[ov.nodes[q]].lab)
-                if (idxU[l] >= 0 && nd.fx[l] < 0) nmask[q] |= 1ull << idxU[l];
-        const int S = pow3[k];
-        std::vector<double> rho(S);
-        std::vector<char> cons(S);
-        for (int s = 0; s < S; s++) {
-            uint64_t fixedm = 0;
-            uint32_t m = 0, vv = 0;
-            int x = s;
-            for (int i = 0; i < k; i++, x /= 3) {
-                int d = x % 3;
-                if (d) {
-                    fixedm |= 1ull << i;
-                    m |= 1u << i;
-                    if (d == 2) { vv |= 1u << i; fixedm |= nbmask[i]; }
-                }
+            for (size_t c = 0; c < cands.size() && c < (size_t)lookahead; c++) {
+                std::vector<int> r2, c2;
+                const double g = branch_at(p, tree_, cap, nd.fx, ov, score, cands[c], K, r2, c2);
+                log->gamma[base + cands[c]] = (float)g;
+                if (g > 0 && g < gbest) { gbest = g; seed = cands[c]; }
             }
-            double r = 0;
-            for (size_t q = 0; q < ov.nodes.size(); q++) {
-                int sz = ov.size[q] - __builtin_popcountll(nmask[q] & fixedm);
-                if (sz > cap) r += sz - cap;
+            log->count++;
+        } else if (learned_branch) {
+            double smax = score[cands[0]];
+            std::vector<float> sc(p.n);
+            for (int v = 0; v < p.n; v++) sc[v] = (float)(score[v] / smax);
+            gnn_features(p.n, p.ei, p.ej, wv, nd.fx, feats, &sc);
+            gnn_branch_->forward(feats.data(), blogit, stream_);
+            const size_t m = std::max<size_t>(lookahead, kGnnBranchCandidates);
+            for (size_t c = 0; c < cands.size() && c < m; c++)
+                if (blogit[cands[c]] > blogit[seed]) seed = cands[c];
+        } else if (lookahead > 1) {
+            double gbest = INFINITY;
+            for (size_t c = 0; c < cands.size() && c < (size_t)lookahead; c++) {
+                std::vector<int> r2, c2;
+                const double g = branch_at(p, tree_, cap, nd.fx, ov, score, cands[c], K, r2, c2);
+                if (g > 0 && g < gbest) { gbest = g; seed = cands[c]; }
             }
-            rho[s] = r;
-            char any = 0;
-            for (uint32_t c : F) if ((c & m) == vv) { any = 1; break; }
-            cons[s] = any;
         }
-        const double rho0 = rho[0];
-        std::vector<double> memo(S);
-        std::vector<int> choice(S);
-        std::vector<int> by_fixed(S);      // states, most fixed variables first
-        {
-            std::vector<int> nfix(S);
-            for (int s = 0; s < S; s++) {
-                int x = s, nf = 0;
-                for (int i = 0; i < k; i++, x /= 3) if (x % 3) nf++;
-                nfix[s] = nf;
-                by_fixed[s] = s;
-            }
-            std::stable_sort(by_fixed.begin(), by_fixed.end(), [&](int a, int b) { return nfix[a] > nfix[b]; });
-        }
-        auto dp = [&](double gamma) {
-            for (int s : by_fixed) {
-                if (!cons[s]) { memo[s] = 0; choice[s] = -1; continue; }
-                double best = s == 0 ? INFINITY : std::pow(gamma, rho[s] - rho0);
-                int bc = -1;
-                int x = s;
-                for (int i = 0; i < k; i++, x /= 3) {
-                    if (x % 3) continue;
-                    double c = memo[s + pow3[i]] + memo[s + 2 * pow3[i]];
-                    if (c < best) { best = c; bc = i; }
-                }
-                memo[s] = best;
-                choice[s] = bc;
-            }
-            return memo[0];
-        };
-        double lo = 1.0, hi = std::ldexp(1.0, k) + 1;
-        for (int it = 0; it < 40; it++) {
-            double mid = std::sqrt(lo * hi);
-            if (dp(mid) <= 1.0) hi = mid; else lo = mid;
-        }
-        dp(hi);
-        std::vector<int> clause_states;
-        std::function<void(int)> collect = [&](int s) {
-            if (!cons[s]) return;
-            if (choice[s] < 0) { clause_states.push_back(s); return; }
-            collect(s + pow3[choice[s]]);
-            collect(s + 2 * pow3[choice[s]]);
-        };
-        collect(0);
+        gamma = branch_at(p, tree_, cap, nd.fx, ov, score, seed, K, R, clause_states);
         st_->t_plan_s += now_s() - tp;
+        if (gamma == 0) { st_->pruned++; continue; }     // F(R) empty: no feasible configuration
+        const int k = (int)R.size();
         // ---- children: fix each clause, propagate, bound
         std::vector<BNode> kids;
         for (int s : clause_states) {
@@ -717,6 +824,12 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
         info->slices_log2 = (int)vf.size();
         for (int v : vf) fx[v] = 0;
     }
+    if (opts_.mode == BBTN_MODE_BBTN) {
+        search(true, nullptr);
+        info->bb_nodes = st.nodes;
+        info->bb_leaves = st.leaves;   // the step list below stays that of the root network
+        if (c.sc > BBTN_MAX_RANK) return;
+    }
     Plan plan = make_plan(tree_, net_, fx, np_, cprime_, false);
     info->steps = (int64_t)plan.steps.size();
     info->ops = plan.ops;
@@ -743,6 +856,13 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
         }
         fclose(f);
     }
+}
+
+void Solver::branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st) {
+    st_ = st;
+    memset(st, 0, sizeof(*st));
+    setup_host(p, false);
+    search(true, log);
 }
 
 SolveOutput Solver::solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st) {

@@ -25,14 +25,31 @@ struct SolveOutput {
     bool have_x = false;
 };
 
+// Per-node records of a dry search (training data of the learned branch scorer).
+struct BranchLog {
+    int max = 0;              // rows available
+    int lookahead = 1;        // candidates the search itself compares
+    int count = 0;            // rows written
+    std::vector<int8_t> fx;   // max x n fixings
+    std::vector<float> score; // max x n overflow score / its maximum
+    std::vector<float> gamma; // max x n: gamma of the branching seeded at v (-1: not a candidate, 0: infeasible)
+};
+
 class Solver {
   public:
     Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena) : opts_(o), stream_(s), arena_(arena) {}
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
     // host-only planning summary (bbtn_analyze)
     void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);
-    // learned branch scorer (used with opts.use_gnn on MWIS instances; borrowed)
-    void set_gnn(GnnModel *g) { gnn_ = g; }
+    // learned scorers (used with opts.use_gnn; borrowed): `branch` picks the seed of
+    // each branching region, `value` predicts an optimum (first incumbent and the
+    // order of children, MWIS only)
+    void set_gnn(GnnModel *branch, GnnModel *value) {
+        gnn_branch_ = branch;
+        gnn_ = value;
+    }
+    // dry search of the loaded problem with per-node lookahead records (host only)
+    void branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st);
 
   private:
     struct Leafset;
@@ -43,6 +60,7 @@ class Solver {
     void run_plain();
     void run_sliced();
     void run_bbtn();
+    void search(bool dry, BranchLog *log);
     int64_t incumbent_heuristic();
     int64_t incumbent_learned();
     void simplify(std::vector<int8_t> &fx) const;
@@ -75,6 +93,7 @@ class Solver {
     Profiler prof_;
     DeviceBuf prog_;                    // fused-subtree programs
     GnnModel *gnn_ = nullptr;
+    GnnModel *gnn_branch_ = nullptr;
     std::vector<float> logit_;          // model logits of x_v = 1 at the root
     void ensure_buffers(int64_t n);
     void release_buffers();

@@ -28,18 +28,23 @@ def _flat_edges(inst):
     return np.ascontiguousarray(np.asarray(inst.edges, dtype=np.int32).reshape(-1))
 
 
-def features(inst, fixed: Optional[Iterable[int]] = None) -> np.ndarray:
-    """Feature rows (n x 8, float32) of an MWIS instance; fixed[v] in {-1, 0, 1}."""
+def features(inst, fixed: Optional[Iterable[int]] = None, score=None) -> np.ndarray:
+    """Feature rows (n x 8, float32); fixed[v] in {-1, 0, 1}; score: overflow shares."""
     lib = _lib.load()
     n = inst.n
     e = _flat_edges(inst)
     w = getattr(inst, "w", None)
+    if inst.kind == "spin":
+        h2 = getattr(inst, "h2", None)
+        w = [abs(int(x)) for x in h2] if h2 is not None else [0] * n
     wv = np.ascontiguousarray(np.asarray(w, dtype=np.int32)) if w is not None else None
+    sv = np.ascontiguousarray(np.asarray(score, dtype=np.float32)) if score is not None else None
     fx = np.ascontiguousarray(np.asarray(fixed, dtype=np.int8)) if fixed is not None else None
     out = np.zeros((n, N_FEATURES), dtype=np.float32)
     check(lib.bbtn_gnn_features(n, len(inst.edges), e.ctypes.data_as(_lib._i32p),
                                 wv.ctypes.data_as(_lib._i32p) if wv is not None else None,
-                                fx.ctypes.data_as(_lib._i8p) if fx is not None else None, _f32(out)))
+                                fx.ctypes.data_as(_lib._i8p) if fx is not None else None,
+                                _f32(sv) if sv is not None else None, _f32(out)))
     return out
 
 
@@ -154,3 +159,64 @@ def mean_loss(model: GNN, data) -> float:
             tot += model.train_step(f, y, m, 0.0)
             cnt += 1
     return tot / max(cnt, 1)
+
+
+# ---------------------------------------------------------------- branch scorer data
+
+def branch_rows(inst, cap: int, max_rows: int, lookahead: int = 16, seed: int = 1):
+    """Training rows of the branch scorer from one instance (host-side search).
+
+    Every expanded node of the lookahead search gives one row: features with the
+    overflow shares, label 1 on the candidate seeds whose branching attains the
+    smallest gamma, mask on the candidates. Rows where all candidates tie carry no
+    signal and are dropped.
+    """
+    from . import Solver
+    s = Solver(space_cap_log2=cap, seed=seed)
+    fx, sc, ga = s.branch_samples(inst, max_rows, lookahead)
+    s.close()
+    out = []
+    for r in range(len(fx)):
+        g = ga[r]
+        cand = g > 0
+        if cand.sum() < 2:
+            continue
+        gmin = g[cand].min()
+        y = (cand & (g <= gmin * (1 + 1e-6))).astype(np.float32)
+        if y.sum() == cand.sum():
+            continue
+        out.append((features(inst, fx[r], sc[r]), y, cand.astype(np.float32)))
+    return out
+
+
+def _rows_job(args):
+    kind, N, seed, cap, max_rows, lookahead = args
+    import synth
+    inst = synth.kings_subgraph(N, 0.8, seed=seed)
+    return inst, branch_rows(inst, cap, max_rows, lookahead)
+
+
+def branch_dataset(specs, workers: int = 0):
+    """[(kind, N, seed, cap, max_rows, lookahead)] -> [(inst, rows)], host processes in parallel."""
+    import multiprocessing as mp
+    import os
+    workers = workers or max(1, (os.cpu_count() or 2) - 1)
+    if workers == 1:
+        return [_rows_job(a) for a in specs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_rows_job, specs, chunksize=1)
+
+
+def top1_agreement(model: GNN, data) -> float:
+    """Fraction of rows whose top-scored candidate is one of the best seeds."""
+    hit = tot = 0
+    for inst, rows in data:
+        if not rows:
+            continue
+        model.set_graph(inst)
+        for f, y, m in rows:
+            s = model.forward(f)
+            s = np.where(m > 0, s, -np.inf)
+            hit += y[int(np.argmax(s))] > 0
+            tot += 1
+    return hit / max(tot, 1)

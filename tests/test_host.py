@@ -147,7 +147,8 @@ def test_gnn_features_match_oracle(P, seed):
     inst = synth.kings_subgraph(9, 0.8, seed=seed, weights="uniform10" if seed else "unit")
     rng = np.random.default_rng(seed)
     fixed = rng.integers(-1, 2, inst.n)
-    got = gnn.features(inst, fixed)
-    want = G.features(inst.n, inst.edges, inst.w, fixed)
+    score = rng.random(inst.n).astype(np.float32) if seed else None
+    got = gnn.features(inst, fixed, score)
+    want = G.features(inst.n, inst.edges, inst.w, fixed, score)
     np.testing.assert_allclose(got, want, rtol=1e-7, atol=0)
     assert gnn.GNN.param_count() == G.param_count()

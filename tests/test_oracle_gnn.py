@@ -47,24 +47,27 @@ def test_gradient_matches_finite_differences(seed):
 
 
 def test_message_passing_closed_form():
-    """Hand-set weights: layer 1 puts deg/8 (own feature 5) and the neighbour sum of
-    the constant feature (= degree) into unit 0; layers 2, 3 pass unit 0 through and
-    add the neighbours' unit 0. Then s_v = 9/8 deg_v + 9/8 * sum_{u~v} deg_u +
-    9/8 * sum_{u~v} (deg_u + sum_{t~u} deg_t) = closed form in A and deg."""
+    """Hand-set weights: layer 1 puts deg/8 (own feature 5), twice the overflow share
+    (feature 7) and the neighbours' deg/8 into unit 0; layers 2, 3 pass unit 0
+    through and add the neighbours' unit 0; the head reads unit 0. With d the
+    degree vector and q the shares: h1 = d/8 + 2q + A d/8, h_{l+1} = h_l + A h_l,
+    s = h3 -- a closed form in the adjacency matrix."""
     inst, A = _graph(3, N=5)
     p = np.zeros(G.param_count())
     layers, w, _ = G.unpack(p)   # views into p
     W1, U1, _ = layers[0]
     W1[5, 0] = 1.0
-    U1[7, 0] = 1.0
+    W1[7, 0] = 2.0
+    U1[5, 0] = 1.0
     for l in (1, 2):
         W, U, _ = layers[l]
         W[0, 0] = 1.0
         U[0, 0] = 1.0
     w[0] = 1.0
-    X = G.features(inst.n, inst.edges)
+    q = np.random.default_rng(4).random(inst.n)
+    X = G.features(inst.n, inst.edges, score=q)
     deg = A.sum(axis=1)
-    h1 = deg / 8.0 + deg
+    h1 = deg / 8.0 + 2 * q + A @ deg / 8.0
     h2 = h1 + A @ h1
     h3 = h2 + A @ h2
     s, _ = G.forward(p, A, X)
@@ -110,11 +113,11 @@ def test_permutation_equivariance():
 
 
 def test_features_by_hand():
-    """Path 0-1-2 with vertex 0 fixed to 1 and weights 5, 20, 3."""
-    X = G.features(3, [(0, 1), (1, 2)], [5, 20, 3], [1, -1, -1])
-    np.testing.assert_allclose(X[0], [0, 0, 1, 0.5, 1 / 8, 1 / 8, 0, 1])
+    """Path 0-1-2 with vertex 0 fixed to 1, weights 5, 20, 3 and shares 0, 1, 0.5."""
+    X = G.features(3, [(0, 1), (1, 2)], [5, 20, 3], [1, -1, -1], [0.0, 1.0, 0.5])
+    np.testing.assert_allclose(X[0], [0, 0, 1, 0.5, 1 / 8, 1 / 8, 0, 0])
     np.testing.assert_allclose(X[1], [1, 0, 0, 2.0, 1 / 8, 2 / 8, 1 / 8, 1])
-    np.testing.assert_allclose(X[2], [1, 0, 0, 0.3, 1 / 8, 1 / 8, 0, 1])
+    np.testing.assert_allclose(X[2], [1, 0, 0, 0.3, 1 / 8, 1 / 8, 0, 0.5])
 
 
 def test_empty_mask_gives_zero_loss_and_gradient():
