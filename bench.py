@@ -160,6 +160,8 @@ def run_ours(args, rank, world, local_rank):
 
     solver = make_solver()
 
+    per_inst_ms = {}
+
     def one_step(step, timed):
         dev_ms, st_sum, h2d, d2h = 0.0, {}, 0, 0
         t0 = time.perf_counter()
@@ -171,6 +173,8 @@ def run_ours(args, rank, world, local_rank):
             eb.record(stream)
             eb.synchronize()
             dev_ms += ea.elapsed_time(eb)
+            if timed:
+                per_inst_ms[idx] = ea.elapsed_time(eb)
             for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms"):
                 st_sum[k] = st_sum.get(k, 0) + res.stats[k]
             h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
@@ -238,6 +242,28 @@ def run_ours(args, rank, world, local_rank):
     dominant = dict(dominant)
     dominant["share_of_contraction_time"] = max(pb["prof_stream_ms"], pb["prof_tiled_ms"]) / max(pb["prof_ms"], 1e-9)
     dominant["other_kernel"] = other
+    # plain tensor-network contraction (dynamic slicing until the cap holds, every
+    # slice contracted, no pruning) on a bounded sample of the timed instances
+    ttn = None
+    if rank == 0 and args.ttn_instances > 0:
+        sl = P.Solver(mode=P.MODE_SLICED, space_cap_log2=CAP, n_primes=3, batch=64, stream=stream.cuda_stream)
+        t_ttn, t_bb, idxs, slices = 0.0, 0.0, [], []
+        for idx, inst in instances(rank, world, 0, per)[:args.ttn_instances]:
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sl.load(inst)
+            ea.record(stream)
+            r = sl.solve(count=True, config=False)
+            eb.record(stream)
+            eb.synchronize()
+            t_ttn += ea.elapsed_time(eb) / 1000.0
+            t_bb += per_inst_ms.get(idx, float("nan")) / 1000.0
+            idxs.append(idx)
+            slices.append(r.stats["slices_log2"])
+        k = len(idxs)
+        ttn = {"value": t_ttn / k, "unit": "s/instance", "instances": idxs, "slices_log2": slices,
+               "bbtn_same_instances": t_bb / k, "bbtn_speedup": t_ttn / t_bb if t_bb else None,
+               "what": "same kernels, dynamic slicing to the same cap, all slices contracted with counts"}
+        sl.close()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, sample = oracle_time(args.cpu_instances)
@@ -256,6 +282,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(stats.get("launches", 0)),
         "tropical_gops": stats.get("tropical_ops", 0) / tot_dev / 1e9 if tot_dev else 0.0,
         "leaves_per_instance": stats.get("leaves", 0) / (per * args.steps),
+        "plain_ttn": ttn,
         "roofline": dominant,
         "clocks": ck,
         "cpu_baseline": cpu,
@@ -319,6 +346,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances-per-step", type=int, default=4)
     ap.add_argument("--cpu-instances", type=int, default=2)
+    ap.add_argument("--ttn-instances", type=int, default=2,
+                    help="timed instances also solved by plain sliced contraction (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the per-launch roofline pass")
