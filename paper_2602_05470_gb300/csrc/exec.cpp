@@ -121,7 +121,8 @@ void Profiler::collect() {
         BBTN_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
         ms += t;
         if (dump)
-            fprintf(dump, "%d,%d,%d,%d,%d,%.0f,%.0f,%.5f,%d\n", r.ra, r.rb, r.rc, r.rs, r.ident, r.bytes, r.ops, t, r.kind);
+            fprintf(dump, "%d,%d,%d,%d,%d,%.0f,%.0f,%.5f,%d,%d\n", r.ra, r.rb, r.rc, r.rs, r.ident, r.bytes, r.ops, t,
+                    r.kind, r.n);
         bytes += r.bytes;
         ops += r.ops;
         launches++;
@@ -293,6 +294,7 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, Fre
         FSub sub;
         sub.first = (int)plan.fsteps.size();
         sub.count = last - first + 1;
+        sub.leaf = 0;
         for (int i = first; i <= last; i++) {
             const PStep &ps = plan.steps[i];
             FStep f;
@@ -525,85 +527,166 @@ DeviceBuf::~DeviceBuf() {
     if (ptr) cudaFree(ptr);
 }
 
+namespace {
+
+struct LaunchTimer {
+    Profiler *pr;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer(Profiler *p, cudaStream_t st) : pr(p), s(st) {
+        if (pr) {
+            a = pr->get();
+            b = pr->get();
+            BBTN_CUDA(cudaEventRecord(a, s));
+        }
+    }
+    void done(double bytes, double ops, const ContractParams *P, int kind, int n) {
+        if (!pr) return;
+        BBTN_CUDA(cudaEventRecord(b, s));
+        int ra = 0, rb = 0, ident = 0, rc = 0, rs = 0;
+        if (P) {
+            for (int i = 0; i < P->rc; i++) { if (P->oA[i] >= 0) ra++; if (P->oB[i] >= 0) rb++; }
+            for (int j = 0; j < P->rs; j++) { if (P->sA[j] >= 0) ra++; if (P->sB[j] >= 0) rb++; }
+            while (ident < P->rc && P->oA[ident] == ident && P->oB[ident] < 0) ident++;
+            rc = P->rc;
+            rs = P->rs;
+        }
+        pr->recs.push_back({a, b, bytes, ops, ra, rb, rc, rs, ident, kind, n});
+    }
+};
+
+}  // namespace
+
+void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net, char *arena, uint64_t stride,
+               int32_t *out_val, uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st,
+               DeviceBuf *prog) {
+    const int nl = (int)plans.size();
+    if (nl == 0) return;
+    if (nl > kBatchMax) fail(BBTN_EINVAL, "run_plans: too many leaves in one batch");
+    const int np = plans[0]->np;
+    Profiler *pr = st ? st->prof : nullptr;
+    // ---- all small subtrees of every leaf in one launch (K5)
+    {
+        std::vector<FStep> fsteps;
+        std::vector<FSub> fsubs;
+        size_t smem = 0;
+        for (int i = 0; i < nl; i++) {
+            const Plan &pl = *plans[i];
+            const int base = (int)fsteps.size();
+            fsteps.insert(fsteps.end(), pl.fsteps.begin(), pl.fsteps.end());
+            for (FSub sub : pl.fsubs) {
+                sub.first += base;
+                sub.leaf = i;
+                fsubs.push_back(sub);
+            }
+            smem = std::max(smem, pl.fused_smem);
+        }
+        if (!fsubs.empty()) {
+            const size_t bs = fsteps.size() * sizeof(FStep);
+            const size_t bsub = fsubs.size() * sizeof(FSub);
+            const size_t off_sub = (bs + 255) & ~(size_t)255;
+            prog->reserve(off_sub + bsub);
+            BBTN_CUDA(cudaMemcpyAsync(prog->ptr, fsteps.data(), bs, cudaMemcpyHostToDevice, s));
+            BBTN_CUDA(cudaMemcpyAsync((char *)prog->ptr + off_sub, fsubs.data(), bsub, cudaMemcpyHostToDevice, s));
+            FusedParams fp{};
+            fp.steps = (const FStep *)prog->ptr;
+            fp.subs = (const FSub *)((char *)prog->ptr + off_sub);
+            fp.nsubs = (int)fsubs.size();
+            fp.net = net.vals;
+            fp.arena = arena;
+            fp.arena_stride = stride;
+            fp.out_val = out_val;
+            fp.out_cnt = out_cnt;
+            fp.out_plane = out_plane;
+            fp.np = np;
+            for (int t2 = 0; t2 < np; t2++) fp.cprime[t2] = plans[0]->steps.empty() ? 0 : plans[0]->steps[0].P.cprime[t2];
+            LaunchTimer lt(pr, s);
+            cudaError_t e = launch_fused(fp, smem, s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("fused kernel: ") + cudaGetErrorString(e));
+            lt.done(0.0, 0.0, nullptr, 1, nl);
+            if (st) st->launches++;
+        }
+    }
+    // ---- the remaining steps in post-order; the step of one tree node for every
+    // leaf of the batch goes out in one launch per kernel
+    const size_t nsteps = plans[0]->steps.size();
+    for (int i = 1; i < nl; i++)
+        if (plans[i]->steps.size() != nsteps) fail(BBTN_ESTATE, "run_plans: plans of different trees");
+    std::vector<ContractParams> tiled, strm;
+    std::vector<double> tb, tops, sb, sops;
+    for (size_t k = 0; k < nsteps; k++) {
+        tiled.clear();
+        strm.clear();
+        double t_bytes = 0, t_ops = 0, s_bytes = 0, s_ops = 0;
+        for (int i = 0; i < nl; i++) {
+            const Plan &pl = *plans[i];
+            const PStep &ps = pl.steps[k];
+            if (ps.node != plans[0]->steps[k].node) fail(BBTN_ESTATE, "run_plans: plans of different trees");
+            if (ps.fused) continue;
+            char *ar = arena + (uint64_t)i * stride;
+            ContractParams P = ps.P;
+            fill_operand(P.A, ps.a, net, ar);
+            P.A.unit_counts = ps.a.kind == 0;
+            if (P.hasB) {
+                fill_operand(P.B, ps.b, net, ar);
+                P.B.unit_counts = ps.b.kind == 0;
+            }
+            if (ps.c.kind == 2) {
+                P.vc = out_val + i;
+                P.cc = out_cnt ? out_cnt + i : nullptr;
+                P.planeC = out_plane;
+            } else {
+                P.vc = (int32_t *)(ar + ps.c.off);
+                P.cc = (uint64_t *)(ar + ps.c.off + count_plane_offset_bytes(P.rc));
+                P.planeC = 1ull << P.rc;
+            }
+            void *scratch = pl.splitk_bytes ? ar + pl.splitk_off : nullptr;
+            if (nl > 1 && !(scratch && splitk_eligible(P))) {
+                if (tiled_eligible(P)) {
+                    tiled.push_back(P);
+                    t_bytes += ps.bytes;
+                    t_ops += ps.ops;
+                    continue;
+                }
+                if (stream4_eligible(P)) {
+                    strm.push_back(P);
+                    s_bytes += ps.bytes;
+                    s_ops += ps.ops;
+                    continue;
+                }
+            }
+            LaunchTimer lt(pr, s);
+            int kind = 0;
+            cudaError_t e = launch_contract(P, s, &kind, scratch, pl.splitk_bytes);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract kernel: ") + cudaGetErrorString(e));
+            lt.done(ps.bytes, ps.ops, &P, kind, 1);
+            if (st) st->launches++;
+        }
+        if (!tiled.empty()) {
+            LaunchTimer lt(pr, s);
+            cudaError_t e = launch_contract_tiled_batch(tiled.data(), (int)tiled.size(), s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("tiled batch: ") + cudaGetErrorString(e));
+            lt.done(t_bytes, t_ops, &tiled[0], 2, (int)tiled.size());
+            if (st) st->launches++;
+        }
+        if (!strm.empty()) {
+            LaunchTimer lt(pr, s);
+            cudaError_t e = launch_contract_stream4_batch(strm.data(), (int)strm.size(), s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("stream batch: ") + cudaGetErrorString(e));
+            lt.done(s_bytes, s_ops, &strm[0], 0, (int)strm.size());
+            if (st) st->launches++;
+        }
+    }
+    if (st)
+        for (const Plan *pl : plans) {
+            st->ops += pl->ops;
+            st->bytes += pl->bytes;
+        }
+}
+
 void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
               uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st, DeviceBuf *prog) {
-    if (!plan.fsubs.empty()) {
-        // all small subtrees in one launch; their results precede every other step
-        const size_t bs = plan.fsteps.size() * sizeof(FStep);
-        const size_t bsub = plan.fsubs.size() * sizeof(FSub);
-        const size_t off_sub = (bs + 255) & ~(size_t)255;
-        prog->reserve(off_sub + bsub);
-        BBTN_CUDA(cudaMemcpyAsync(prog->ptr, plan.fsteps.data(), bs, cudaMemcpyHostToDevice, s));
-        BBTN_CUDA(cudaMemcpyAsync((char *)prog->ptr + off_sub, plan.fsubs.data(), bsub, cudaMemcpyHostToDevice, s));
-        FusedParams fp{};
-        fp.steps = (const FStep *)prog->ptr;
-        fp.subs = (const FSub *)((char *)prog->ptr + off_sub);
-        fp.nsubs = (int)plan.fsubs.size();
-        fp.net = net.vals;
-        fp.arena = arena;
-        fp.out_val = out_val;
-        fp.out_cnt = out_cnt;
-        fp.out_plane = out_plane;
-        fp.np = plan.np;
-        for (int t2 = 0; t2 < plan.np; t2++) fp.cprime[t2] = plan.steps.empty() ? 0 : plan.steps[0].P.cprime[t2];
-        Profiler *pr = st ? st->prof : nullptr;
-        cudaEvent_t ea = nullptr, eb = nullptr;
-        if (pr) {
-            ea = pr->get();
-            eb = pr->get();
-            BBTN_CUDA(cudaEventRecord(ea, s));
-        }
-        cudaError_t e = launch_fused(fp, plan.fused_smem, s);
-        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("fused kernel: ") + cudaGetErrorString(e));
-        if (pr) {
-            BBTN_CUDA(cudaEventRecord(eb, s));
-            pr->recs.push_back({ea, eb, 0.0, 0.0, 0, 0, 0, 0, 0, 1});
-        }
-        if (st) st->launches++;
-    }
-    for (const PStep &ps : plan.steps) {
-        if (ps.fused) continue;
-        ContractParams P = ps.P;
-        fill_operand(P.A, ps.a, net, arena);
-        P.A.unit_counts = ps.a.kind == 0;
-        if (P.hasB) {
-            fill_operand(P.B, ps.b, net, arena);
-            P.B.unit_counts = ps.b.kind == 0;
-        }
-        if (ps.c.kind == 2) {
-            P.vc = out_val;
-            P.cc = out_cnt;
-            P.planeC = out_plane;
-        } else {
-            P.vc = (int32_t *)(arena + ps.c.off);
-            P.cc = (uint64_t *)(arena + ps.c.off + count_plane_offset_bytes(P.rc));
-            P.planeC = 1ull << P.rc;
-        }
-        Profiler *pr = st ? st->prof : nullptr;
-        cudaEvent_t ea = nullptr, eb = nullptr;
-        if (pr) {
-            ea = pr->get();
-            eb = pr->get();
-            BBTN_CUDA(cudaEventRecord(ea, s));
-        }
-        int kind = 0;
-        cudaError_t e = launch_contract(P, s, &kind, plan.splitk_bytes ? arena + plan.splitk_off : nullptr,
-                                        plan.splitk_bytes);
-        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract kernel: ") + cudaGetErrorString(e));
-        if (pr) {
-            BBTN_CUDA(cudaEventRecord(eb, s));
-            int ra = 0, rb = 0, ident = 0;
-            for (int i = 0; i < P.rc; i++) { if (P.oA[i] >= 0) ra++; if (P.oB[i] >= 0) rb++; }
-            for (int j = 0; j < P.rs; j++) { if (P.sA[j] >= 0) ra++; if (P.sB[j] >= 0) rb++; }
-            while (ident < P.rc && P.oA[ident] == ident && P.oB[ident] < 0) ident++;
-            pr->recs.push_back({ea, eb, ps.bytes, ps.ops, ra, rb, P.rc, P.rs, ident, kind});
-        }
-        if (st) st->launches++;
-    }
-    if (st) {
-        st->ops += plan.ops;
-        st->bytes += plan.bytes;
-    }
+    run_plans({&plan}, net, arena, 0, out_val, out_cnt, out_plane, s, st, prog);
 }
 
 void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net, char *arena,

@@ -78,7 +78,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
 // Per-launch CUDA-event timing of contraction kernels (profile mode): an event
 // pair on the launching stream around each launch, read back after a sync.
 struct Profiler {
-    struct Rec { cudaEvent_t a, b; double bytes, ops; int ra, rb, rc, rs, ident, kind; };
+    struct Rec { cudaEvent_t a, b; double bytes, ops; int ra, rb, rc, rs, ident, kind, n; };
     FILE *dump = nullptr;    // optional CSV of every launch (BBTN_PROFILE_DUMP)
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> recs;
@@ -111,6 +111,15 @@ struct DeviceBuf {
 // program while it runs (stream-ordered reuse across plans).
 void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *out_val,
               uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st, DeviceBuf *prog);
+
+// Enqueue the plans of up to kBatchMax leaf sub-networks of one tree together:
+// leaf i uses the arena at arena + i * stride and writes its root result to
+// (out_val[i], out_cnt[t * out_plane + i]). The fused subtrees of every leaf run in
+// one launch; each remaining tree node runs as one launch per kernel for all
+// leaves (paper Eq. (3): the leaves are the sliced sub-networks of one network).
+void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net, char *arena, uint64_t stride,
+               int32_t *out_val, uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st,
+               DeviceBuf *prog);
 
 // Backward walk after run_plan with keep_all: sets x[v] for every free variable
 // (fixed ones copied from fx). Synchronises the stream.

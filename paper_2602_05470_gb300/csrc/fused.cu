@@ -18,6 +18,7 @@ template <int NP>
 __global__ void __launch_bounds__(kThr) k_fused(const __grid_constant__ FusedParams p) {
     extern __shared__ __align__(16) unsigned char sm[];
     const FSub sub = p.subs[blockIdx.x];
+    char *const arena = p.arena + (uint64_t)sub.leaf * p.arena_stride;
     for (int si = sub.first; si < sub.first + sub.count; si++) {
         const FStep &st = p.steps[si];
         const int rc = st.rc, rs = st.rs;
@@ -36,12 +37,12 @@ __global__ void __launch_bounds__(kThr) k_fused(const __grid_constant__ FusedPar
             cc = (uint64_t *)(sm + st.c_off + smem_count_offset(rc));
             cplane = nout;
         } else if (st.c_kind == 2) {
-            cv = (int32_t *)(p.arena + st.c_goff);
-            cc = (uint64_t *)(p.arena + st.c_goff + (((4ull << rc) + 255) & ~255ull));
+            cv = (int32_t *)(arena + st.c_goff);
+            cc = (uint64_t *)(arena + st.c_goff + (((4ull << rc) + 255) & ~255ull));
             cplane = nout;
         } else {
-            cv = p.out_val;
-            cc = p.out_cnt;
+            cv = p.out_val + sub.leaf;
+            cc = p.out_cnt ? p.out_cnt + sub.leaf : nullptr;
             cplane = p.out_plane;
         }
         const uint32_t aplane = 1u << st.a_rank, bplane = 1u << st.b_rank;

@@ -418,6 +418,8 @@ __global__ void k_fill(int32_t *val, uint64_t *cnt, uint64_t n, uint64_t plane, 
 
 cudaError_t launch_contract_stream(const ContractParams &p, cudaStream_t s) {
     if (p.rc < 0 || p.rc > 30 || p.rs < 0 || p.rs > 40) return cudaErrorInvalidValue;
+    cudaError_t e = launch_contract_stream4(p, s);
+    if (e != cudaErrorNotSupported) return e;
     return p.hasB ? dispatch_contract<true>(p, s) : dispatch_contract<false>(p, s);
 }
 

@@ -44,8 +44,19 @@ size_t splitk_scratch_bytes(int rc, int np);
 cudaError_t launch_contract_splitk(const ContractParams &p, void *scratch, size_t bytes, cudaStream_t s);
 // K1t only; cudaErrorNotSupported when the step's shape does not fit it.
 cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s);
-// K1 / K3 only.
+// K1 / K3 only (four outputs per thread when rc >= 2, else one).
 cudaError_t launch_contract_stream(const ContractParams &p, cudaStream_t s);
+// K1v: four consecutive outputs per thread; cudaErrorNotSupported when rc < 2.
+cudaError_t launch_contract_stream4(const ContractParams &p, cudaStream_t s);
+bool stream4_eligible(const ContractParams &p);
+
+// Leaf-batched launches: the same tree node's step of up to kBatchMax leaf
+// sub-networks in one launch, each entry with its own operands, output and shape
+// (all entries: same np and hasB). cudaErrorNotSupported if an entry does not fit.
+constexpr int kBatchMax = 16;
+cudaError_t launch_contract_stream4_batch(const ContractParams *p, int n, cudaStream_t s);
+cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s);
+bool tiled_eligible(const ContractParams &p);
 
 // out bit q <- in bit perm[q]
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,
@@ -74,6 +85,7 @@ struct FStep {
 };
 struct FSub {
     int first, count;                  // its steps, in post-order
+    int leaf;                          // leaf sub-network: arena + leaf * arena_stride, out_* + leaf
 };
 struct FusedParams {
     const FStep *steps;
@@ -81,6 +93,7 @@ struct FusedParams {
     int nsubs;
     const int32_t *net;
     char *arena;
+    uint64_t arena_stride;             // bytes between the arenas of consecutive leaves
     int32_t *out_val;
     uint64_t *out_cnt;
     uint64_t out_plane;

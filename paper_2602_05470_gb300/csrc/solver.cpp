@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstring>
 #include <cstdlib>
+#include <exception>
 #include <functional>
+#include <thread>
 
 #include "common.h"
 
@@ -274,6 +276,32 @@ double branch_at(const Problem &p, const CTree &tree, int cap, const std::vector
 
 }  // namespace
 
+namespace {
+
+// f(0..n-1) on up to 16 host threads; the first exception is rethrown here.
+void parallel_for(int64_t n, const std::function<void(int64_t)> &f) {
+    const int64_t nt = std::min<int64_t>({n, 16, std::max<int64_t>(1, std::thread::hardware_concurrency())});
+    if (nt <= 1) {
+        for (int64_t i = 0; i < n; i++) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    std::vector<std::exception_ptr> err(nt);
+    for (int64_t t = 0; t < nt; t++)
+        th.emplace_back([&, t] {
+            try {
+                for (int64_t i = t; i < n; i += nt) f(i);
+            } catch (...) {
+                err[t] = std::current_exception();
+            }
+        });
+    for (auto &x : th) x.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
+}
+
+}  // namespace
+
 void Solver::ensure_buffers(int64_t n) {
     // slots 0..n-1 plus one temporary slot at index dcap_; slot 0 (the running
     // counting-sum) survives a reallocation
@@ -358,6 +386,10 @@ void Solver::simplify(std::vector<int8_t> &fx) const {
 
 void Solver::setup(const Problem &p, bool want_count) {
     setup_host(p, want_count);
+    // device memory the leaf arenas of one launch group may take: half of what is free
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
+        arena_budget_ = (uint64_t)(free_b + (arena_->owned ? arena_->size : 0)) / 2;
     net_.upload(stream_);
     release_buffers();
     ensure_buffers(std::max(opts_.batch, 1) + 1);
@@ -426,16 +458,27 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
     rs.prof = opts_.profile ? &prof_ : nullptr;
     if (rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
         prof_.dump = fopen(getenv("BBTN_PROFILE_DUMP"), "w");
-        if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms,kind\n");
+        if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms,kind,n\n");
     }
-    for (int64_t i = 0; i < n; i++) {
-        const double tp = now_s();
-        Plan plan = make_plan(tree_, net_, leaves[i], counting ? np_ : 0, cprime_, false);
-        st_->t_plan_s += now_s() - tp;
-        arena_->reserve(plan.arena_bytes);
-        st_->sc_log2 = std::max(st_->sc_log2, plan.max_rank);
-        st_->steps += (int64_t)plan.steps.size();
-        run_plan(plan, net_, arena_->ptr, d_val_ + 1 + i, d_cnt_ + 1 + i, plane, stream_, &rs, &prog_);
+    // plan every leaf (host threads), then run them in groups that share launches:
+    // leaf i of a group gets its own arena at i * stride
+    const double tp = now_s();
+    std::vector<Plan> plans(n);
+    parallel_for(n, [&](int64_t i) { plans[i] = make_plan(tree_, net_, leaves[i], counting ? np_ : 0, cprime_, false); });
+    st_->t_plan_s += now_s() - tp;
+    uint64_t stride = 256;
+    for (const Plan &pl : plans) {
+        stride = std::max<uint64_t>(stride, (pl.arena_bytes + 255) & ~255ull);
+        st_->sc_log2 = std::max(st_->sc_log2, pl.max_rank);
+        st_->steps += (int64_t)pl.steps.size();
+    }
+    const uint64_t budget = arena_->owned ? std::max<uint64_t>(arena_budget_, arena_->size) : arena_->size;
+    const int64_t nb = std::max<int64_t>(1, std::min<int64_t>({(int64_t)kBatchMax, (int64_t)(budget / stride), n}));
+    arena_->reserve(stride * nb);
+    for (int64_t i0 = 0; i0 < n; i0 += nb) {
+        std::vector<const Plan *> group;
+        for (int64_t i = i0; i < std::min(n, i0 + nb); i++) group.push_back(&plans[i]);
+        run_plans(group, net_, arena_->ptr, stride, d_val_ + 1 + i0, d_cnt_ + 1 + i0, plane, stream_, &rs, &prog_);
     }
     if (counting) {
         // slot 0 <- counting-sum of slots 0..n

@@ -82,6 +82,7 @@ class Solver {
     int32_t *d_val_ = nullptr;
     uint64_t *d_cnt_ = nullptr;
     int64_t dcap_ = 0;
+    uint64_t arena_budget_ = 1ull << 30;   // bytes the leaf arenas of one launch group may use
     void *d_scratch_ = nullptr;
     size_t scratch_bytes_ = 0;
     // best leaf (for the configuration)

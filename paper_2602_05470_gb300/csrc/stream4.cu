@@ -1,0 +1,282 @@
+// K1v: the streaming gather contraction (K1 / K3, paper Eq. (2), one binary step
+// of contract(T)) with four consecutive outputs per thread.
+//
+//   C[o] = max(NEG, max_s A[offA(o) + kA(s)] + B[offB(o) + kB(s)])   with counts
+//
+// Most steps of a tree are bound by HBM bandwidth: a big tensor meets a small
+// one (an edge matrix or a small intermediate) and the summed extent is 1-16.
+// One output per thread leaves too few loads in flight to cover HBM latency, so
+// each thread owns outputs 4q..4q+3 and issues all of their loads for a summed
+// assignment together. When the two lowest output bits are A's two lowest bits
+// (the layout policy puts pass-through labels low), the four A values are one
+// 128-bit load and the four results one 128-bit store. Offsets are 32-bit: every
+// operand has at most 2^30 elements.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace bbtn {
+
+namespace {
+
+constexpr int kThr = 256;
+constexpr int kKTab = 12;   // summed extent tabulated in shared memory (2^12 entries)
+
+__device__ __forceinline__ uint32_t tab4(const uint32_t (*t)[256], uint32_t o) {
+    return t[0][o & 255] + t[1][(o >> 8) & 255] + t[2][(o >> 16) & 255] + t[3][o >> 24];
+}
+
+template <bool HASB>
+__device__ __forceinline__ void build_tables(const ContractParams &P, uint32_t (*tA)[256], uint32_t (*tB)[256],
+                                             uint32_t *kA, uint32_t *kB, int ktb) {
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        const int ch = i >> 8, v = i & 255;
+        uint32_t a = 0, b = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int bit = ch * 8 + j;
+            if (bit < P.rc && ((v >> j) & 1)) {
+                if (P.oA[bit] >= 0) a += 1u << P.oA[bit];
+                if (HASB && P.oB[bit] >= 0) b += 1u << P.oB[bit];
+            }
+        }
+        tA[ch][v] = a;
+        tB[ch][v] = b;
+    }
+    for (uint32_t k = threadIdx.x; k < (1u << ktb); k += blockDim.x) {
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < ktb; j++)
+            if ((k >> j) & 1) {
+                if (P.sA[j] >= 0) a += 1u << P.sA[j];
+                if (HASB && P.sB[j] >= 0) b += 1u << P.sB[j];
+            }
+        kA[k] = a;
+        kB[k] = b;
+    }
+}
+
+// offsets of the summed bits above the tabulated ones for the high index hi
+__device__ __forceinline__ void hi_offsets(const ContractParams &P, int ktb, uint32_t hi, uint32_t &ah,
+                                           uint32_t &bh) {
+    for (int j = ktb; j < P.rs; j++)
+        if ((hi >> (j - ktb)) & 1) {
+            if (P.sA[j] >= 0) ah += 1u << P.sA[j];
+            if (P.sB[j] >= 0) bh += 1u << P.sB[j];
+        }
+}
+
+template <int NP, bool HASB>
+__device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA, int vecC, uint32_t bid,
+                                               uint32_t nblk, uint32_t (*tA)[256], uint32_t (*tB)[256],
+                                               uint32_t *ktab) {
+    const int ktb = P.rs < kKTab ? P.rs : kKTab;
+    const uint32_t KT = 1u << ktb;
+    uint32_t *kA = ktab, *kB = ktab + KT;
+    build_tables<HASB>(P, tA, tB, kA, kB, ktb);
+    __syncthreads();
+
+    // offsets of output bits 0 and 1 (outputs 4q + j differ from 4q by these)
+    const uint32_t dA1 = tA[0][1], dA2 = tA[0][2], dA3 = tA[0][3];
+    const uint32_t dB1 = tB[0][1], dB2 = tB[0][2], dB3 = tB[0][3];
+    const bool bconst = !HASB || (dB1 | dB2 | dB3) == 0;
+    const uint32_t nhi = 1u << (P.rs - ktb);
+    const int32_t *__restrict__ va = P.A.val + P.A.base;
+    const int32_t *__restrict__ vb = HASB ? P.B.val + P.B.base : nullptr;
+    const uint64_t nq = 1ull << (P.rc - 2);
+    const uint64_t stride = (uint64_t)nblk * blockDim.x;
+
+    for (uint64_t q = (uint64_t)bid * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        const uint32_t o = (uint32_t)q << 2;
+        const uint32_t ao = tab4(tA, o);
+        const uint32_t bo = HASB ? tab4(tB, o) : 0u;
+        int32_t best[4] = {kNeg, kNeg, kNeg, kNeg};
+        for (uint32_t hi = 0; hi < nhi; hi++) {
+            uint32_t ah = ao, bh = bo;
+            if (hi) hi_offsets(P, ktb, hi, ah, bh);
+#pragma unroll 2
+            for (uint32_t k = 0; k < KT; k++) {
+                const uint32_t ea = ah + kA[k];
+                int32_t a[4], b[4] = {0, 0, 0, 0};
+                if (vecA) {
+                    const int4 x = __ldg((const int4 *)(va + ea));
+                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                } else {
+                    a[0] = __ldg(va + ea);
+                    a[1] = __ldg(va + ea + dA1);
+                    a[2] = __ldg(va + ea + dA2);
+                    a[3] = __ldg(va + ea + dA3);
+                }
+                if (HASB) {
+                    const uint32_t eb = bh + kB[k];
+                    b[0] = __ldg(vb + eb);
+                    if (bconst) {
+                        b[1] = b[2] = b[3] = b[0];
+                    } else {
+                        b[1] = __ldg(vb + eb + dB1);
+                        b[2] = __ldg(vb + eb + dB2);
+                        b[3] = __ldg(vb + eb + dB3);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) best[j] = max(best[j], a[j] + b[j]);
+            }
+        }
+        if (vecC) {
+            *(int4 *)(P.vc + o) = make_int4(best[0], best[1], best[2], best[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) P.vc[o + j] = best[j];
+        }
+        if constexpr (NP > 0) {
+            // second pass: sum the count products of the maximising assignments
+            const uint32_t dA[4] = {0u, dA1, dA2, dA3}, dB[4] = {0u, dB1, dB2, dB3};
+            uint64_t acc[4][NP];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int t = 0; t < NP; t++) acc[j][t] = 0;
+            const bool any = best[0] >= kFiniteMin || best[1] >= kFiniteMin || best[2] >= kFiniteMin ||
+                             best[3] >= kFiniteMin;
+            for (uint32_t hi = 0; any && hi < nhi; hi++) {
+                uint32_t ah = ao, bh = bo;
+                if (hi) hi_offsets(P, ktb, hi, ah, bh);
+                for (uint32_t k = 0; k < KT; k++) {
+                    const uint32_t ea = ah + kA[k];
+                    const uint32_t eb = HASB ? bh + kB[k] : 0u;
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        if (best[j] < kFiniteMin) continue;
+                        const uint32_t ej = ea + dA[j];
+                        const int32_t av = __ldg(va + ej);
+                        const int32_t bv = HASB ? __ldg(vb + eb + dB[j]) : 0;
+                        if (av + bv != best[j]) continue;
+#pragma unroll
+                        for (int t = 0; t < NP; t++) {
+                            const uint32_t c = P.cprime[t];
+                            uint64_t term;
+                            if (P.A.unit_counts) {
+                                term = (HASB && !P.B.unit_counts)
+                                           ? __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j])
+                                           : 1ull;
+                            } else {
+                                const uint64_t x = __ldg(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ej);
+                                if (!HASB || P.B.unit_counts) term = x;
+                                else term = mulmod61(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
+                            }
+                            acc[j][t] = addmod61(acc[j][t], term, c);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < NP; t++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) P.cc[(uint64_t)t * P.planeC + o + j] = acc[j][t];
+        }
+    }
+}
+
+
+// One launch runs the same step of up to NB leaf sub-networks (each with its own
+// operands, output and shape): block b belongs to entry e with blk0[e] <= b <
+// blk0[e + 1]. NB = 1 is the plain single-step launch.
+template <int NB>
+struct S4Args {
+    int n;
+    uint32_t blk0[NB + 1];
+    int8_t vecA[NB], vecC[NB];
+    ContractParams p[NB];
+};
+
+template <int NP, bool HASB, int NB>
+__global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Args<NB> args) {
+    __shared__ uint32_t tA[4][256];
+    __shared__ uint32_t tB[4][256];
+    extern __shared__ uint32_t ktab[];
+    if constexpr (NB == 1) {
+        contract4_body<NP, HASB>(args.p[0], args.vecA[0], args.vecC[0], blockIdx.x, gridDim.x, tA, tB, ktab);
+    } else {
+        __shared__ ContractParams sP;
+        int e = 0;
+        while (e + 1 < args.n && blockIdx.x >= args.blk0[e + 1]) e++;
+        const uint32_t *src = (const uint32_t *)&args.p[e];
+        for (int i = threadIdx.x; i < (int)(sizeof(ContractParams) / 4); i += blockDim.x) ((uint32_t *)&sP)[i] = src[i];
+        __syncthreads();
+        contract4_body<NP, HASB>(sP, args.vecA[e], args.vecC[e], blockIdx.x - args.blk0[e],
+                                 args.blk0[e + 1] - args.blk0[e], tA, tB, ktab);
+    }
+}
+
+template <int NP, bool HASB, int NB>
+cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
+    S4Args<NB> a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    int ktb = 0;
+    uint64_t total = 0;
+    for (int i = 0; i < n; i++) {
+        const ContractParams &p = ps[i];
+        ktb = std::max(ktb, p.rs < kKTab ? p.rs : kKTab);
+        const uint64_t nq = 1ull << (p.rc - 2);
+        uint64_t blocks = (nq + kThr - 1) / kThr;
+        const uint64_t cap = 152ull * 8;
+        if (blocks > cap) blocks = cap;
+        a.blk0[i] = (uint32_t)total;
+        total += blocks;
+        const int32_t *a0 = p.A.val + p.A.base;
+        a.vecA[i] = p.oA[0] == 0 && p.oA[1] == 1 && ((uintptr_t)a0 & 15) == 0;
+        a.vecC[i] = ((uintptr_t)p.vc & 15) == 0;
+        a.p[i] = p;
+    }
+    a.blk0[n] = (uint32_t)total;
+    const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << ktb);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_contract4<NP, HASB, NB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_contract4<NP, HASB, NB><<<(unsigned)total, kThr, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool HASB, int NB>
+cudaError_t dispatch4(const ContractParams *p, int n, cudaStream_t s) {
+    switch (p[0].np) {
+        case 0: return launch4<0, HASB, NB>(p, n, s);
+        case 1: return launch4<1, HASB, NB>(p, n, s);
+        case 2: return launch4<2, HASB, NB>(p, n, s);
+        case 3: return launch4<3, HASB, NB>(p, n, s);
+        case 4: return launch4<4, HASB, NB>(p, n, s);
+        case 5: return launch4<5, HASB, NB>(p, n, s);
+        case 6: return launch4<6, HASB, NB>(p, n, s);
+        case 7: return launch4<7, HASB, NB>(p, n, s);
+        case 8: return launch4<8, HASB, NB>(p, n, s);
+        case 9: return launch4<9, HASB, NB>(p, n, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool fits4(const ContractParams &p) { return p.rc >= 2 && p.rc <= 30 && p.rs >= 0 && p.rs <= 30; }
+
+}  // namespace
+
+cudaError_t launch_contract_stream4(const ContractParams &p, cudaStream_t s) {
+    if (!fits4(p)) return cudaErrorNotSupported;
+    return p.hasB ? dispatch4<true, 1>(&p, 1, s) : dispatch4<false, 1>(&p, 1, s);
+}
+
+bool stream4_eligible(const ContractParams &p) { return fits4(p); }
+
+cudaError_t launch_contract_stream4_batch(const ContractParams *p, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (n > kBatchMax) return cudaErrorInvalidValue;
+    for (int i = 0; i < n; i++)
+        if (!fits4(p[i]) || p[i].np != p[0].np || p[i].hasB != p[0].hasB) return cudaErrorNotSupported;
+    if (n == 1) return p[0].hasB ? dispatch4<true, 1>(p, 1, s) : dispatch4<false, 1>(p, 1, s);
+    return p[0].hasB ? dispatch4<true, kBatchMax>(p, n, s) : dispatch4<false, kBatchMax>(p, n, s);
+}
+
+}  // namespace bbtn

@@ -14,6 +14,8 @@
 // output's count or adds the products of the chunk's maximising k.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "kernels.h"
 
 namespace bbtn {
@@ -69,9 +71,8 @@ __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const u
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1)
-k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups G, int fastA_k, int fastB_k) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups &G, int fastA_k, int fastB_k,
+                                           uint64_t tile, unsigned char *smem_raw) {
     // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
     // sB[TK][TN+4], counts
     const int K = 1 << G.nk;
@@ -88,7 +89,6 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
 
     const int mt = 1 << (G.nm > 6 ? G.nm - 6 : 0);
     const int nt = 1 << (G.nn > 6 ? G.nn - 6 : 0);
-    const uint64_t tile = blockIdx.x;
     const int tn = (int)(tile % nt);
     const int tm = (int)((tile / nt) % mt);
     const uint64_t b = tile / ((uint64_t)nt * mt);
@@ -238,6 +238,37 @@ k_tiled(const __grid_constant__ ContractParams P, const __grid_constant__ Groups
     }
 }
 
+// One launch runs the same step of up to NB leaf sub-networks: block b belongs to
+// entry e with blk0[e] <= b < blk0[e + 1] (its tile is b - blk0[e]). NB = 1 is the
+// plain single-step launch.
+template <int NB>
+struct TArgs {
+    int n;
+    uint32_t blk0[NB + 1];
+    int8_t fa[NB], fb[NB];
+    ContractParams p[NB];
+    Groups g[NB];
+};
+
+template <int NP, int NB>
+__global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (NB == 1) {
+        tiled_body<NP>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
+    } else {
+        __shared__ ContractParams sP;
+        __shared__ Groups sG;
+        int e = 0;
+        while (e + 1 < args.n && blockIdx.x >= args.blk0[e + 1]) e++;
+        const uint32_t *src = (const uint32_t *)&args.p[e];
+        for (int i = threadIdx.x; i < (int)(sizeof(ContractParams) / 4); i += blockDim.x) ((uint32_t *)&sP)[i] = src[i];
+        const unsigned char *gsrc = (const unsigned char *)&args.g[e];
+        for (int i = threadIdx.x; i < (int)sizeof(Groups); i += blockDim.x) ((unsigned char *)&sG)[i] = gsrc[i];
+        __syncthreads();
+        tiled_body<NP>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
+    }
+}
+
 size_t tiled_smem(int nk, int np) {
     (void)nk;
     size_t s = 2 * 768 * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
@@ -245,24 +276,35 @@ size_t tiled_smem(int nk, int np) {
     return s;
 }
 
-template <int NP>
-cudaError_t launch_t(const ContractParams &p, const Groups &g, int fa, int fb, cudaStream_t s) {
-    const size_t smem = tiled_smem(g.nk, NP);
-    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int NP, int NB>
+cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, const int *fb, int n, cudaStream_t s) {
+    TArgs<NB> a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    uint64_t total = 0;
+    for (int i = 0; i < n; i++) {
+        const Groups &g = gs[i];
+        a.blk0[i] = (uint32_t)total;
+        total += (1ull << g.nb) * (1ull << (g.nm - 6)) * (1ull << (g.nn - 6));
+        if (total > 0x7fffffffull) return cudaErrorInvalidValue;
+        a.p[i] = ps[i];
+        a.g[i] = g;
+        a.fa[i] = (int8_t)fa[i];
+        a.fb[i] = (int8_t)fb[i];
+    }
+    a.blk0[n] = (uint32_t)total;
+    const size_t smem = tiled_smem(0, NP);
+    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const uint64_t blocks = (1ull << g.nb) * (1ull << (g.nm - 6)) * (1ull << (g.nn - 6));
-    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-    k_tiled<NP><<<(unsigned)blocks, kThr, smem, s>>>(p, g, fa, fb);
+    k_tiled<NP, NB><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-// Decide whether a step fits the tiled kernel and, if so, launch it.
-// Returns cudaErrorNotSupported when the step has to take the streaming kernel.
-cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
-    if (!p.hasB || p.np > 4) return cudaErrorNotSupported;
-    Groups g{};
+// Splits the labels of a step into the kernel's groups; false when the step does
+// not fit the tiled kernel (it then takes the streaming kernel).
+bool make_groups(const ContractParams &p, Groups &g, int &fa, int &fb) {
+    if (!p.hasB || p.np > 4) return false;
+    memset(&g, 0, sizeof g);
     int bitA0 = -1, bitB0 = -1;   // which group holds bit 0 of A / B
     for (int i = 0; i < p.rc; i++) {
         const int a = p.oA[i], b = p.oB[i];
@@ -283,17 +325,51 @@ cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
         g.kB[g.nk] = p.sB[j];
         g.nk++;
     }
-    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 24) return cudaErrorNotSupported;
+    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 24) return false;
     // lanes along k when the operand's bit 0 is a summed label, else along m / n
-    const int fa = bitA0 == 0, fb = bitB0 == 0;
-    switch (p.np) {
-        case 0: return launch_t<0>(p, g, fa, fb, s);
-        case 1: return launch_t<1>(p, g, fa, fb, s);
-        case 2: return launch_t<2>(p, g, fa, fb, s);
-        case 3: return launch_t<3>(p, g, fa, fb, s);
-        case 4: return launch_t<4>(p, g, fa, fb, s);
+    fa = bitA0 == 0;
+    fb = bitB0 == 0;
+    return true;
+}
+
+template <int NB>
+cudaError_t dispatch_t(const ContractParams *p, const Groups *g, const int *fa, const int *fb, int n, cudaStream_t s) {
+    switch (p[0].np) {
+        case 0: return launch_t<0, NB>(p, g, fa, fb, n, s);
+        case 1: return launch_t<1, NB>(p, g, fa, fb, n, s);
+        case 2: return launch_t<2, NB>(p, g, fa, fb, n, s);
+        case 3: return launch_t<3, NB>(p, g, fa, fb, n, s);
+        case 4: return launch_t<4, NB>(p, g, fa, fb, n, s);
         default: return cudaErrorNotSupported;
     }
+}
+
+}  // namespace
+
+bool tiled_eligible(const ContractParams &p) {
+    Groups g;
+    int fa, fb;
+    return make_groups(p, g, fa, fb);
+}
+
+// Decide whether a step fits the tiled kernel and, if so, launch it.
+// Returns cudaErrorNotSupported when the step has to take the streaming kernel.
+cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
+    Groups g;
+    int fa, fb;
+    if (!make_groups(p, g, fa, fb)) return cudaErrorNotSupported;
+    return dispatch_t<1>(&p, &g, &fa, &fb, 1, s);
+}
+
+cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (n > kBatchMax) return cudaErrorInvalidValue;
+    Groups g[kBatchMax];
+    int fa[kBatchMax], fb[kBatchMax];
+    for (int i = 0; i < n; i++)
+        if (p[i].np != p[0].np || !make_groups(p[i], g[i], fa[i], fb[i])) return cudaErrorNotSupported;
+    if (n == 1) return dispatch_t<1>(p, g, fa, fb, 1, s);
+    return dispatch_t<kBatchMax>(p, g, fa, fb, n, s);
 }
 
 }  // namespace bbtn

@@ -294,3 +294,53 @@ def test_contract_tiled_long_sum(P):
     vc, cc = _run(P, la, A, lb, B, lc, primes)
     ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
     assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+
+
+# Paths of the four-outputs-per-thread streaming kernel: 128-bit loads of A when
+# the two lowest output bits are A's two lowest bits and A is 16-byte aligned,
+# scalar loads otherwise; 128-bit stores when C is 16-byte aligned; B constant or
+# varying over the four outputs; summed labels at A's low bits; reductions.
+VEC = [
+    # (la, lb, lc, shift_a, shift_c)
+    (list(range(16)), [15, 16], list(range(15)) + [16], 0, 0),        # growth step, summed top bit
+    (list(range(16)), [15, 16], list(range(15)) + [16], 1, 0),        # A not 16-byte aligned
+    (list(range(16)), [15, 16], list(range(15)) + [16], 0, 3),        # C not 16-byte aligned
+    (list(range(14)), [3, 20], list(range(14)) + [20], 1, 1),         # no summed label, both shifted
+    (list(range(14)), [0, 20], [20] + list(range(1, 14)), 0, 0),      # low output bit from B, A's bit 0 summed
+    ([30] + list(range(14)), [30, 31], list(range(14)) + [31], 0, 0),  # summed label at A's bit 0
+    (list(range(15)), [0, 1, 40], list(range(15)) + [40], 0, 0),      # B varies over the low bits
+    (list(range(12)) + [50, 51], None, list(range(12)), 1, 2),         # single-operand reduction, shifted
+    (list(range(12)) + [50, 51], None, list(range(12)), 0, 0),         # single-operand reduction, aligned
+    (list(range(2, 17)) + [0, 1], [0, 1, 60], list(range(2, 17)) + [60], 0, 0),  # summed at A's top bits
+]
+
+
+@pytest.mark.parametrize("case", range(len(VEC)))
+@pytest.mark.parametrize("np_", [0, 4])
+def test_contract_vector_paths(P, case, np_):
+    la, lb, lc, sa, sc = VEC[case]
+    rng = np.random.default_rng(700 + case)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), neg_frac=0.1)
+    A = (A[0], A[1][:np_])
+    va_full = torch.zeros((1 << len(la)) + sa, dtype=torch.int32, device="cuda")
+    va_full[sa:] = torch.from_numpy(A[0]).cuda()
+    va = va_full[sa:]
+    ca = torch.from_numpy(A[1].view(np.int64)).cuda() if np_ else None
+    if lb is None:
+        B = (None, np.zeros((np_, 0), np.uint64))
+        vb = cb = None
+    else:
+        B = _rand(rng, len(lb), max(np_, 1), neg_frac=0.1)
+        B = (B[0], B[1][:np_])
+        vb, cb = _dev(*B)
+        if not np_:
+            cb = None
+    vc_full = torch.zeros((1 << len(lc)) + sc, dtype=torch.int32, device="cuda")
+    cc = torch.zeros((np_, 1 << len(lc)), dtype=torch.int64, device="cuda") if np_ else None
+    P.contract(la, va, ca, lb, vb, cb, lc, primes, out=(vc_full[sc:], cc))
+    torch.cuda.synchronize()
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc_full[sc:].cpu().numpy(), ov)
+    if np_:
+        assert np.array_equal(cc.cpu().numpy().view(np.uint64), oc)
