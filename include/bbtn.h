@@ -140,6 +140,19 @@ int bbtn_aggregate_noalloc(int64_t n, const int32_t *vals, const uint64_t *count
 size_t bbtn_aggregate_noalloc_max_scratch(void);
 
 /*
+ * Value-only variant of bbtn_contract (same step, paper Eq. (2), no counts) for
+ * operands whose finite values all lie in (-2^12, 2^12): the register-tiled
+ * kernel then adds and maxes two 16-bit lanes per instruction (the solver uses
+ * this for its value-only leaves when the instance's total value range allows
+ * it). Every feasible output (>= BBTN_FINITE_MIN) equals bbtn_contract's; an
+ * infeasible output is some value below BBTN_FINITE_MIN (BBTN_NEG from the 16-bit
+ * kernel). Finite inputs outside the range give undefined feasible results.
+ * Arguments as for bbtn_contract with np = 0; device pointers; asynchronous.
+ */
+int bbtn_contract_values16(int ra, const int32_t *la, const int32_t *va, int rb, const int32_t *lb,
+                           const int32_t *vb, int rc, const int32_t *lc, int32_t *vc, void *stream);
+
+/*
  * Tropical back-propagation through one pairwise step (the backward pass that
  * recovers an optimal configuration): for each of `q` selected output entries
  * sel_o[i] of C = contract(A, B) (values only), find the smallest summed

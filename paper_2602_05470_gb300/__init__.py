@@ -23,7 +23,7 @@ from . import _lib
 from ._lib import (BBTNError, FINITE_MIN, MAX_PRIMES, MODE_BBTN, MODE_PLAIN, MODE_SLICED, NEG,  # noqa: F401
                    Opts, Stats, check, i32_array, u64_array)
 
-__all__ = ["primes", "crt", "contract", "permute", "aggregate", "contract_backward", "Solver", "Result",
+__all__ = ["primes", "crt", "contract", "contract_values16", "permute", "aggregate", "contract_backward", "Solver", "Result",
            "BBTNError", "NEG", "FINITE_MIN", "MODE_PLAIN", "MODE_SLICED", "MODE_BBTN", "lib_path"]
 
 
@@ -84,6 +84,19 @@ def contract(la, va, ca, lb, vb, cb, lc, primes_, out=None, stream=None):
                             rc, i32_array(lc), _ptr(vc), _ptr(cc), np_, u64_array(primes_),
                             _stream(stream)))
     return vc, cc
+
+
+def contract_values16(la, va, lb, vb, lc, out=None, stream=None):
+    """Value-only contraction with 16-bit lanes for operands whose finite values lie
+    in (-2^12, 2^12); feasible outputs equal contract()'s, infeasible ones are below
+    FINITE_MIN. lb=None: single-operand reduction."""
+    import torch
+    lib = _lib.load()
+    vc = torch.empty(1 << len(lc), dtype=torch.int32, device=va.device) if out is None else out
+    rb = 0 if lb is None else len(lb)
+    check(lib.bbtn_contract_values16(len(la), i32_array(la), _ptr(va), rb, i32_array(lb or []), _ptr(vb),
+                                     len(lc), i32_array(lc), _ptr(vc), _stream(stream)))
+    return vc
 
 
 def permute(perm, vin, cin, stream=None):

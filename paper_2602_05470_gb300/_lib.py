@@ -73,6 +73,7 @@ _SIGS = {
     "bbtn_crt_decimal": ([C.c_int, _u64p, _u64p, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_contract": ([C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp,
                        C.c_int, _u64p, _vp], C.c_int),
+    "bbtn_contract_values16": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, _vp], C.c_int),
     "bbtn_permute": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
     "bbtn_aggregate": ([C.c_int64, _vp, _vp, C.c_int, _u64p, _vp, _vp, _vp], C.c_int),
     "bbtn_contract_backward": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp,

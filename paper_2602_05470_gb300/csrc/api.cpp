@@ -110,9 +110,11 @@ int bbtn_crt_decimal(int k, const uint64_t *res, const uint64_t *primes, char *b
     });
 }
 
-int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca, int rb,
-                  const int32_t *lb, const int32_t *vb, const uint64_t *cb, int rc, const int32_t *lc,
-                  int32_t *vc, uint64_t *cc, int np, const uint64_t *primes, void *stream) {
+namespace {
+
+int contract_impl(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca, int rb, const int32_t *lb,
+                  const int32_t *vb, const uint64_t *cb, int rc, const int32_t *lc, int32_t *vc, uint64_t *cc,
+                  int np, const uint64_t *primes, int v16, void *stream) {
     return guarded([&] {
         check_labels(ra, la, "A");
         check_labels(rb, lb, "B");
@@ -147,6 +149,7 @@ int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *
         P.rc = rc;
         P.rs = rs;
         P.np = np;
+        P.v16 = v16;
         P.hasB = rb > 0 || vb != nullptr;
         P.A.val = va;
         P.A.cnt = ca;
@@ -172,6 +175,19 @@ int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *
         if (scratch) cudaFreeAsync(scratch, s);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("contract: ") + cudaGetErrorString(e));
     });
+}
+
+}  // namespace
+
+int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca, int rb,
+                  const int32_t *lb, const int32_t *vb, const uint64_t *cb, int rc, const int32_t *lc,
+                  int32_t *vc, uint64_t *cc, int np, const uint64_t *primes, void *stream) {
+    return contract_impl(ra, la, va, ca, rb, lb, vb, cb, rc, lc, vc, cc, np, primes, 0, stream);
+}
+
+int bbtn_contract_values16(int ra, const int32_t *la, const int32_t *va, int rb, const int32_t *lb,
+                           const int32_t *vb, int rc, const int32_t *lc, int32_t *vc, void *stream) {
+    return contract_impl(ra, la, va, nullptr, rb, lb, vb, nullptr, rc, lc, vc, nullptr, 0, nullptr, 1, stream);
 }
 
 int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin, int32_t *vout,

@@ -149,10 +149,15 @@ void DeviceNetwork::set_host(const std::vector<TensorDef> &ts, int nv) {
     offset.resize(ts.size());
     labels.resize(ts.size());
     host_vals.clear();
+    value_bound = 0;
     for (size_t i = 0; i < ts.size(); i++) {
         offset[i] = host_vals.size();
         labels[i] = ts[i].labels;
         host_vals.insert(host_vals.end(), ts[i].val.begin(), ts[i].val.end());
+        int64_t m = 0;
+        for (int32_t v : ts[i].val)
+            if (v >= kFiniteMin) m = std::max<int64_t>(m, v < 0 ? -(int64_t)v : v);
+        value_bound += m;
     }
     if (host_vals.empty()) host_vals.push_back(0);
 }
@@ -438,6 +443,9 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
         P.rs = (int)sum.size();
         P.hasB = B != nullptr;
         P.np = np;
+        // every finite entry of an intermediate is a sum of one entry per network
+        // tensor, so |value| <= value_bound: 16-bit lanes are exact below 2^12
+        P.v16 = np == 0 && net.value_bound < (1 << 12);
         for (int t2 = 0; t2 < np; t2++) P.cprime[t2] = cprime[t2];
         for (int i = 0; i < 32; i++) P.oA[i] = P.oB[i] = P.sA[i] = P.sB[i] = -1;
         for (int i = 0; i < P.rc; i++) {

@@ -20,6 +20,8 @@ struct DeviceNetwork {
     std::vector<uint64_t> offset;            // element offset of tensor i
     std::vector<std::vector<int>> labels;    // bit i <-> labels[i]
     std::vector<int32_t> host_vals;          // staged values (set_host), uploaded by upload()
+    int64_t value_bound = 0;                 // sum over tensors of the largest |finite entry|:
+                                             // bounds |value| of every intermediate entry
     void set_host(const std::vector<TensorDef> &ts, int nvars);
     void upload(cudaStream_t s);
     void release();

@@ -30,6 +30,10 @@ struct ContractParams {
     int rc = 0, rs = 0, hasB = 0, np = 0;
     int8_t oA[32], oB[32], sA[32], sB[32];
     uint32_t cprime[kMaxPlanes];
+    // value-only steps: 1 if every finite value of both operands and of the result
+    // is known to lie in (-2^13, 2^13) -- the tiled kernel then adds and maxes two
+    // 16-bit values per instruction (int32 in memory, infeasible results as NEG)
+    int v16 = 0;
 };
 
 // Picks the kernel: the register-tiled one (K1t) for large two-operand steps, else

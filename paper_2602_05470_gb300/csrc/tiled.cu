@@ -70,7 +70,14 @@ __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const u
     }
 }
 
-template <int NP>
+// 16-bit lanes of the packed value-only path: infeasible entries enter as -2^14, so
+// no sum of two entries leaves the int16 range; a result below -2^13 is infeasible.
+constexpr int32_t kNeg16 = -(1 << 14);
+constexpr int32_t kFinite16 = -(1 << 13);
+__device__ __forceinline__ int32_t to16(int32_t x) { return x >= kFiniteMin ? x : kNeg16; }
+__device__ __forceinline__ uint32_t dup16(int32_t x) { return ((uint32_t)x & 0xffffu) | ((uint32_t)x << 16); }
+
+template <int NP, bool V16>
 __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups &G, int fastA_k, int fastB_k,
                                            uint64_t tile, unsigned char *smem_raw) {
     // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
@@ -119,7 +126,61 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
         for (int j = 0; j < 4; j++) best[i][j] = kNeg;
 
-    if constexpr (NP == 0) {
+    if constexpr (V16) {
+        // values only, two 16-bit lanes per instruction: A is stored duplicated into
+        // both halves, B as int16 pairs along n; the next chunk is prefetched into
+        // registers while the current one is computed
+        uint16_t(*sB16)[TN + 8] = (uint16_t(*)[TN + 8])sB;
+        uint32_t best2[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; i++) best2[i][0] = best2[i][1] = dup16(kNeg16);
+        int32_t ra[4], rb[4];
+        auto gload = [&](int k0) {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int e = threadIdx.x + r * kThr;
+                const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
+                ra[r] = __ldg(P.A.val + baseA + rowA[mi] + kof(koffA, k0 + ki));
+                const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
+                rb[r] = __ldg(P.B.val + baseB + colB[nj] + kof(koffB, k0 + kj));
+            }
+        };
+        auto sstore = [&]() {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int e = threadIdx.x + r * kThr;
+                const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
+                sA[ki][mi] = (int32_t)dup16(to16(ra[r]));
+                const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
+                sB16[kj][nj] = (uint16_t)to16(rb[r]);
+            }
+        };
+        gload(0);
+        for (int k0 = 0; k0 < K; k0 += TK) {
+            __syncthreads();
+            sstore();
+            __syncthreads();
+            if (k0 + TK < K) gload(k0 + TK);
+#pragma unroll
+            for (int kk = 0; kk < TK; kk++) {
+                const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
+                const uint2 b2 = *(const uint2 *)&sB16[kk][tx * 4];
+                const uint32_t a[4] = {(uint32_t)a4.x, (uint32_t)a4.y, (uint32_t)a4.z, (uint32_t)a4.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    best2[i][0] = __viaddmax_s16x2(a[i], b2.x, best2[i][0]);
+                    best2[i][1] = __viaddmax_s16x2(a[i], b2.y, best2[i][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int32_t r = (int32_t)(int16_t)(best2[i][j >> 1] >> (16 * (j & 1)));
+                P.vc[baseC + rowC[ty * 4 + i] + colC[tx * 4 + j]] = r >= kFinite16 ? r : kNeg;
+            }
+    } else if constexpr (NP == 0) {
         // values only: int32 add + max. The next chunk's tiles are fetched into
         // registers while the current chunk is computed from shared memory.
         {
@@ -250,11 +311,11 @@ struct TArgs {
     Groups g[NB];
 };
 
-template <int NP, int NB>
+template <int NP, int NB, bool V16>
 __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
-        tiled_body<NP>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
+        tiled_body<NP, V16>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
     } else {
         __shared__ ContractParams sP;
         __shared__ Groups sG;
@@ -265,7 +326,7 @@ __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_co
         const unsigned char *gsrc = (const unsigned char *)&args.g[e];
         for (int i = threadIdx.x; i < (int)sizeof(Groups); i += blockDim.x) ((unsigned char *)&sG)[i] = gsrc[i];
         __syncthreads();
-        tiled_body<NP>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
+        tiled_body<NP, V16>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
     }
 }
 
@@ -276,7 +337,7 @@ size_t tiled_smem(int nk, int np) {
     return s;
 }
 
-template <int NP, int NB>
+template <int NP, int NB, bool V16>
 cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, const int *fb, int n, cudaStream_t s) {
     TArgs<NB> a;
     memset(&a, 0, sizeof a);
@@ -294,9 +355,9 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
     }
     a.blk0[n] = (uint32_t)total;
     const size_t smem = tiled_smem(0, NP);
-    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tiled<NP, NB><<<(unsigned)total, kThr, smem, s>>>(a);
+    k_tiled<NP, NB, V16><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -335,11 +396,11 @@ bool make_groups(const ContractParams &p, Groups &g, int &fa, int &fb) {
 template <int NB>
 cudaError_t dispatch_t(const ContractParams *p, const Groups *g, const int *fa, const int *fb, int n, cudaStream_t s) {
     switch (p[0].np) {
-        case 0: return launch_t<0, NB>(p, g, fa, fb, n, s);
-        case 1: return launch_t<1, NB>(p, g, fa, fb, n, s);
-        case 2: return launch_t<2, NB>(p, g, fa, fb, n, s);
-        case 3: return launch_t<3, NB>(p, g, fa, fb, n, s);
-        case 4: return launch_t<4, NB>(p, g, fa, fb, n, s);
+        case 0: return p[0].v16 ? launch_t<0, NB, true>(p, g, fa, fb, n, s) : launch_t<0, NB, false>(p, g, fa, fb, n, s);
+        case 1: return launch_t<1, NB, false>(p, g, fa, fb, n, s);
+        case 2: return launch_t<2, NB, false>(p, g, fa, fb, n, s);
+        case 3: return launch_t<3, NB, false>(p, g, fa, fb, n, s);
+        case 4: return launch_t<4, NB, false>(p, g, fa, fb, n, s);
         default: return cudaErrorNotSupported;
     }
 }
@@ -367,7 +428,8 @@ cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStre
     Groups g[kBatchMax];
     int fa[kBatchMax], fb[kBatchMax];
     for (int i = 0; i < n; i++)
-        if (p[i].np != p[0].np || !make_groups(p[i], g[i], fa[i], fb[i])) return cudaErrorNotSupported;
+        if (p[i].np != p[0].np || p[i].v16 != p[0].v16 || !make_groups(p[i], g[i], fa[i], fb[i]))
+            return cudaErrorNotSupported;
     if (n == 1) return dispatch_t<1>(p, g, fa, fb, 1, s);
     return dispatch_t<kBatchMax>(p, g, fa, fb, n, s);
 }

@@ -344,3 +344,29 @@ def test_contract_vector_paths(P, case, np_):
     assert np.array_equal(vc_full[sc:].cpu().numpy(), ov)
     if np_:
         assert np.array_equal(cc.cpu().numpy().view(np.uint64), oc)
+
+
+@pytest.mark.parametrize("case", range(len(TILED) + 2))
+def test_contract_values16(P, case):
+    """16-bit-lane value-only contraction: feasible outputs equal the oracle's,
+    infeasible ones stay below FINITE_MIN. Values span (-2^12, 2^12)."""
+    if case < len(TILED):
+        la, lb, lc = _tiled_case(*TILED[case])
+    else:
+        la, lb, lc = CASES[8 + case - len(TILED)][:3]
+    rng = np.random.default_rng(900 + case)
+    va = rng.integers(-2000, 2000, size=1 << len(la)).astype(np.int32)
+    vb = rng.integers(-2000, 2000, size=1 << len(lb)).astype(np.int32)
+    # enough infeasible entries that both feasible and infeasible outputs occur
+    frac = 0.9 if case < len(TILED) else 0.3
+    va[rng.random(va.size) < frac] = oracle.NEG
+    vb[rng.random(vb.size) < frac] = oracle.NEG
+    vc = P.contract_values16(la, torch.from_numpy(va).cuda(), lb, torch.from_numpy(vb).cuda(), lc)
+    torch.cuda.synchronize()
+    got = vc.cpu().numpy()
+    ov, _ = oracle.contract(la, va, np.zeros((0, va.size), np.uint64), lb, vb, np.zeros((0, vb.size), np.uint64),
+                            lc, [])
+    feas = ov >= -(1 << 28)
+    assert feas.any() and (~feas).any()
+    assert np.array_equal(got[feas], ov[feas])
+    assert (got[~feas] < -(1 << 28)).all()
