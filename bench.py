@@ -300,6 +300,9 @@ KERNEL_CASES = {
               list(range(0, 11)) + list(range(40, 51)) + [60, 61], 0),
     "tiled_count": (list(range(0, 10)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 50)) + [60, 61],
                     list(range(0, 10)) + list(range(40, 50)) + [60, 61], 4),
+    # the same big x big step with 16-bit lanes (value-only leaves of small-range instances)
+    "tiled16": (list(range(0, 11)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 51)) + [60, 61],
+                list(range(0, 11)) + list(range(40, 51)) + [60, 61], -1),
 }
 
 
@@ -308,6 +311,8 @@ def run_kernel_case(args):
     import torch
     import paper_2602_05470_gb300 as P
     la, lb, lc, np_ = KERNEL_CASES[args.kernel_case]
+    v16 = np_ < 0
+    np_ = max(np_, 0)
     gen = torch.Generator(device="cuda").manual_seed(0)
     va = torch.randint(-4, 4, (1 << len(la),), dtype=torch.int32, device="cuda", generator=gen)
     vb = torch.randint(-4, 4, (1 << len(lb),), dtype=torch.int32, device="cuda", generator=gen)
@@ -316,13 +321,19 @@ def run_kernel_case(args):
     primes = P.primes(np_)
     out = (torch.empty(1 << len(lc), dtype=torch.int32, device="cuda"),
            torch.empty((np_, 1 << len(lc)), dtype=torch.int64, device="cuda") if np_ else None)
+    def step():
+        if v16:
+            P.contract_values16(la, va, lb, vb, lc, out=out[0])
+        else:
+            P.contract(la, va, ca, lb, vb, cb, lc, primes, out=out)
+
     for _ in range(args.warmup):
-        P.contract(la, va, ca, lb, vb, cb, lc, primes, out=out)
+        step()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     ev[0].record()
     for _ in range(args.steps):
-        P.contract(la, va, ca, lb, vb, cb, lc, primes, out=out)
+        step()
     ev[1].record()
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1]) / args.steps

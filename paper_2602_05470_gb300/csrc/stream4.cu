@@ -68,8 +68,17 @@ __device__ __forceinline__ void hi_offsets(const ContractParams &P, int ktb, uin
         }
 }
 
+// The four outputs of a thread differ in two output bits g1 < g2 (the group bits).
+// The host picks output bits that A does not carry when there are any: outputs
+// that differ only there read the same A entries, so A leaves HBM once.
+struct Group4 {
+    int8_t g1, g2;     // group bits
+    int8_t vecA;       // g = (0, 1) are A's bits 0, 1 and A is 16-byte aligned: one 128-bit load
+    int8_t vecC;       // g = (0, 1) and C is 16-byte aligned: one 128-bit store
+};
+
 template <int NP, bool HASB>
-__device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA, int vecC, uint32_t bid,
+__device__ __forceinline__ void contract4_body(const ContractParams &P, const Group4 gr, uint32_t bid,
                                                uint32_t nblk, uint32_t (*tA)[256], uint32_t (*tB)[256],
                                                uint32_t *ktab) {
     const int ktb = P.rs < kKTab ? P.rs : kKTab;
@@ -78,10 +87,15 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA
     build_tables<HASB>(P, tA, tB, kA, kB, ktb);
     __syncthreads();
 
-    // offsets of output bits 0 and 1 (outputs 4q + j differ from 4q by these)
-    const uint32_t dA1 = tA[0][1], dA2 = tA[0][2], dA3 = tA[0][3];
-    const uint32_t dB1 = tB[0][1], dB2 = tB[0][2], dB3 = tB[0][3];
-    const bool bconst = !HASB || (dB1 | dB2 | dB3) == 0;
+    const int g1 = gr.g1, g2 = gr.g2;
+    const int vecA = gr.vecA, vecC = gr.vecC;
+    // offsets of the group bits in A, B and C (outputs of a thread differ by these)
+    const uint32_t dA1 = P.oA[g1] >= 0 ? 1u << P.oA[g1] : 0u, dA2 = P.oA[g2] >= 0 ? 1u << P.oA[g2] : 0u;
+    const uint32_t dB1 = HASB && P.oB[g1] >= 0 ? 1u << P.oB[g1] : 0u, dB2 = HASB && P.oB[g2] >= 0 ? 1u << P.oB[g2] : 0u;
+    const uint32_t dA3 = dA1 + dA2, dB3 = dB1 + dB2;
+    const uint32_t dC1 = 1u << g1, dC2 = 1u << g2, dC3 = dC1 + dC2;
+    const bool aconst = (dA1 | dA2) == 0;
+    const bool bconst = !HASB || (dB1 | dB2) == 0;
     const uint32_t nhi = 1u << (P.rs - ktb);
     const int32_t *__restrict__ va = P.A.val + P.A.base;
     const int32_t *__restrict__ vb = HASB ? P.B.val + P.B.base : nullptr;
@@ -89,7 +103,10 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA
     const uint64_t stride = (uint64_t)nblk * blockDim.x;
 
     for (uint64_t q = (uint64_t)bid * blockDim.x + threadIdx.x; q < nq; q += stride) {
-        const uint32_t o = (uint32_t)q << 2;
+        // zero bits inserted at g1, then at g2
+        uint32_t o = (uint32_t)q;
+        o = ((o >> g1) << (g1 + 1)) | (o & ((1u << g1) - 1u));
+        o = ((o >> g2) << (g2 + 1)) | (o & ((1u << g2) - 1u));
         const uint32_t ao = tab4(tA, o);
         const uint32_t bo = HASB ? tab4(tB, o) : 0u;
         int32_t best[4] = {kNeg, kNeg, kNeg, kNeg};
@@ -103,6 +120,8 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA
                 if (vecA) {
                     const int4 x = __ldg((const int4 *)(va + ea));
                     a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                } else if (aconst) {
+                    a[0] = a[1] = a[2] = a[3] = __ldg(va + ea);
                 } else {
                     a[0] = __ldg(va + ea);
                     a[1] = __ldg(va + ea + dA1);
@@ -127,8 +146,10 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA
         if (vecC) {
             *(int4 *)(P.vc + o) = make_int4(best[0], best[1], best[2], best[3]);
         } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++) P.vc[o + j] = best[j];
+            P.vc[o] = best[0];
+            P.vc[o + dC1] = best[1];
+            P.vc[o + dC2] = best[2];
+            P.vc[o + dC3] = best[3];
         }
         if constexpr (NP > 0) {
             // second pass: sum the count products of the maximising assignments
@@ -172,9 +193,11 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, int vecA
                 }
             }
 #pragma unroll
+            const uint32_t dC[4] = {0u, dC1, dC2, dC3};
+#pragma unroll
             for (int t = 0; t < NP; t++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) P.cc[(uint64_t)t * P.planeC + o + j] = acc[j][t];
+                for (int j = 0; j < 4; j++) P.cc[(uint64_t)t * P.planeC + o + dC[j]] = acc[j][t];
         }
     }
 }
@@ -187,7 +210,7 @@ template <int NB>
 struct S4Args {
     int n;
     uint32_t blk0[NB + 1];
-    int8_t vecA[NB], vecC[NB];
+    Group4 g[NB];
     ContractParams p[NB];
 };
 
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Ar
     __shared__ uint32_t tB[4][256];
     extern __shared__ uint32_t ktab[];
     if constexpr (NB == 1) {
-        contract4_body<NP, HASB>(args.p[0], args.vecA[0], args.vecC[0], blockIdx.x, gridDim.x, tA, tB, ktab);
+        contract4_body<NP, HASB>(args.p[0], args.g[0], blockIdx.x, gridDim.x, tA, tB, ktab);
     } else {
         __shared__ ContractParams sP;
         int e = 0;
@@ -205,9 +228,27 @@ __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Ar
         const uint32_t *src = (const uint32_t *)&args.p[e];
         for (int i = threadIdx.x; i < (int)(sizeof(ContractParams) / 4); i += blockDim.x) ((uint32_t *)&sP)[i] = src[i];
         __syncthreads();
-        contract4_body<NP, HASB>(sP, args.vecA[e], args.vecC[e], blockIdx.x - args.blk0[e],
+        contract4_body<NP, HASB>(sP, args.g[e], blockIdx.x - args.blk0[e],
                                  args.blk0[e + 1] - args.blk0[e], tA, tB, ktab);
     }
+}
+
+// Group bits: output bits that A does not carry first (they would make A be read
+// once per value), then the lowest remaining bits.
+Group4 pick_group(const ContractParams &p) {
+    int g[2], ng = 0;
+    for (int b = 0; b < p.rc && ng < 2; b++)
+        if (p.oA[b] < 0) g[ng++] = b;
+    for (int b = 0; b < p.rc && ng < 2; b++)
+        if (p.oA[b] >= 0) g[ng++] = b;
+    Group4 r;
+    r.g1 = (int8_t)std::min(g[0], g[1]);
+    r.g2 = (int8_t)std::max(g[0], g[1]);
+    const bool low = r.g1 == 0 && r.g2 == 1;
+    const int32_t *a0 = p.A.val + p.A.base;
+    r.vecA = low && p.oA[0] == 0 && p.oA[1] == 1 && ((uintptr_t)a0 & 15) == 0;
+    r.vecC = low && ((uintptr_t)p.vc & 15) == 0;
+    return r;
 }
 
 template <int NP, bool HASB, int NB>
@@ -226,9 +267,7 @@ cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
         if (blocks > cap) blocks = cap;
         a.blk0[i] = (uint32_t)total;
         total += blocks;
-        const int32_t *a0 = p.A.val + p.A.base;
-        a.vecA[i] = p.oA[0] == 0 && p.oA[1] == 1 && ((uintptr_t)a0 & 15) == 0;
-        a.vecC[i] = ((uintptr_t)p.vc & 15) == 0;
+        a.g[i] = pick_group(p);
         a.p[i] = p;
     }
     a.blk0[n] = (uint32_t)total;

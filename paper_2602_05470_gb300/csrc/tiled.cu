@@ -45,27 +45,46 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, const int8_t *pos, int n
     return r;
 }
 
-// load a TM x TK tile of A (rows m, columns k) into smem as [k][m]
-template <bool VALS, int NP>
-__device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
-                                          uint64_t plane, int unit, uint64_t base, const uint32_t *rowoff,
-                                          const uint32_t *koff, int k0, int fast_k, int32_t (*sv)[TM + 4],
-                                          uint64_t (*sc)[TK][TM + 2]) {
-    // 1024 elements, 4 per thread; lanes run along the operand's contiguous group
+// Per-thread part of a tile load: the thread fetches elements e = tid + r * 256
+// (r < 4) of every TM x TK chunk, with lanes along the operand's contiguous group.
+// Row / column offsets and the in-chunk k offsets do not change from chunk to
+// chunk, so they are summed once; a chunk only adds the deposit of its first k.
+struct Lanes {
+    uint32_t off[4];    // element offset of (row, k in chunk)
+    uint32_t sidx[4];   // shared-memory index ki * (T + 4) + mi
+};
+
+__device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32_t *koff, int fast_k, Lanes &L) {
 #pragma unroll
     for (int r = 0; r < 4; r++) {
         const int e = threadIdx.x + r * kThr;
-        int mi, ki;
-        if (fast_k) { ki = e & (TK - 1); mi = e >> 4; }
-        else { mi = e & (TM - 1); ki = e >> 6; }
-        const uint64_t off = base + rowoff[mi] + kof(koff, k0 + ki);
+        const int mi = fast_k ? (e >> 4) : (e & (TM - 1));
+        const int ki = fast_k ? (e & (TK - 1)) : (e >> 6);
+        L.off[r] = rowoff[mi] + koff[ki];       // ki < 16: first byte table only
+        L.sidx[r] = (uint32_t)(ki * (TM + 4) + mi);
+    }
+}
+
+// chunk offset: deposit of k0's bits (k0 is a multiple of TK, so its bits are
+// disjoint from the in-chunk ones and the deposits add)
+__device__ __forceinline__ uint32_t chunk_off(const uint32_t *koff, int k0) { return kof(koff, (uint32_t)k0); }
+
+// load one chunk of values (and counts) into shared memory as [k][m]
+template <int NP>
+__device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
+                                          uint64_t plane, int unit, const Lanes &L, uint32_t kb,
+                                          int32_t *sv, uint64_t (*sc)[TK][TM + 2]) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const uint32_t off = L.off[r] + kb;
         const int32_t x = __ldg(v + off);
-        if (VALS) sv[ki][mi] = x;
+        sv[L.sidx[r]] = x;
         if constexpr (NP > 0) {
+            uint64_t *scf = &sc[0][0][0];
 #pragma unroll
             for (int t = 0; t < NP; t++)
-                sc[t][ki][mi] = unit ? (x >= kFiniteMin ? 1ull : 0ull) : __ldg(c + (uint64_t)t * plane + off);
-            sv[ki][mi] = x;
+                scf[t * TK * (TM + 2) + (L.sidx[r] / (TM + 4)) * (TM + 2) + L.sidx[r] % (TM + 4)] =
+                    unit ? (x >= kFiniteMin ? 1ull : 0ull) : __ldg(c + (uint64_t)t * plane + off);
         }
     }
 }
@@ -119,6 +138,14 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     }
     __syncthreads();
 
+    Lanes LA, LB;
+    lanes_setup(rowA, koffA, fastA_k, LA);
+    lanes_setup(colB, koffB, fastB_k, LB);
+    const int32_t *__restrict__ Av = P.A.val + baseA;
+    const int32_t *__restrict__ Bv = P.B.val + baseB;
+    const uint64_t *__restrict__ Ac = P.A.cnt ? P.A.cnt + baseA : nullptr;
+    const uint64_t *__restrict__ Bc = P.B.cnt ? P.B.cnt + baseB : nullptr;
+
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 each
     int32_t best[4][4];
 #pragma unroll
@@ -136,23 +163,21 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         for (int i = 0; i < 4; i++) best2[i][0] = best2[i][1] = dup16(kNeg16);
         int32_t ra[4], rb[4];
         auto gload = [&](int k0) {
+            const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
             for (int r = 0; r < 4; r++) {
-                const int e = threadIdx.x + r * kThr;
-                const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
-                ra[r] = __ldg(P.A.val + baseA + rowA[mi] + kof(koffA, k0 + ki));
-                const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
-                rb[r] = __ldg(P.B.val + baseB + colB[nj] + kof(koffB, k0 + kj));
+                ra[r] = __ldg(Av + LA.off[r] + ka);
+                rb[r] = __ldg(Bv + LB.off[r] + kb);
             }
         };
+        int32_t *sAf = &sA[0][0];
+        uint16_t *sB16f = &sB16[0][0];
         auto sstore = [&]() {
 #pragma unroll
             for (int r = 0; r < 4; r++) {
-                const int e = threadIdx.x + r * kThr;
-                const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
-                sA[ki][mi] = (int32_t)dup16(to16(ra[r]));
-                const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
-                sB16[kj][nj] = (uint16_t)to16(rb[r]);
+                sAf[LA.sidx[r]] = (int32_t)dup16(to16(ra[r]));
+                // same (k, n) position in the int16 tile, whose rows are TN + 8 wide
+                sB16f[(LB.sidx[r] / (TN + 4)) * (TN + 8) + LB.sidx[r] % (TN + 4)] = (uint16_t)to16(rb[r]);
             }
         };
         gload(0);
@@ -186,23 +211,19 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         {
             int32_t ra[4], rb[4];
             auto gload = [&](int k0) {
+                const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
-                    const int e = threadIdx.x + r * kThr;
-                    const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
-                    ra[r] = __ldg(P.A.val + baseA + rowA[mi] + kof(koffA, k0 + ki));
-                    const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
-                    rb[r] = __ldg(P.B.val + baseB + colB[nj] + kof(koffB, k0 + kj));
+                    ra[r] = __ldg(Av + LA.off[r] + ka);
+                    rb[r] = __ldg(Bv + LB.off[r] + kb);
                 }
             };
+            int32_t *sAf = &sA[0][0], *sBf = &sB[0][0];
             auto sstore = [&]() {
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
-                    const int e = threadIdx.x + r * kThr;
-                    const int mi = fastA_k ? (e >> 4) : (e & (TM - 1)), ki = fastA_k ? (e & (TK - 1)) : (e >> 6);
-                    sA[ki][mi] = ra[r];
-                    const int nj = fastB_k ? (e >> 4) : (e & (TN - 1)), kj = fastB_k ? (e & (TK - 1)) : (e >> 6);
-                    sB[kj][nj] = rb[r];
+                    sAf[LA.sidx[r]] = ra[r];
+                    sBf[LB.sidx[r]] = rb[r];
                 }
             };
             gload(0);
@@ -240,10 +261,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                 for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
         for (int k0 = 0; k0 < K; k0 += TK) {
-            load_tile<true, NP>(P.A.val, P.A.cnt, P.A.plane, P.A.unit_counts, baseA, rowA, koffA, k0, fastA_k,
-                                sA, cA);
-            load_tile<true, NP>(P.B.val, P.B.cnt, P.B.plane, P.B.unit_counts, baseB, colB, koffB, k0, fastB_k,
-                                sB, cB);
+            load_tile<NP>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], cA);
+            load_tile<NP>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], cB);
             __syncthreads();
             int32_t cm[4][4];
 #pragma unroll

@@ -312,6 +312,9 @@ VEC = [
     (list(range(12)) + [50, 51], None, list(range(12)), 1, 2),         # single-operand reduction, shifted
     (list(range(12)) + [50, 51], None, list(range(12)), 0, 0),         # single-operand reduction, aligned
     (list(range(2, 17)) + [0, 1], [0, 1, 60], list(range(2, 17)) + [60], 0, 0),  # summed at A's top bits
+    (list(range(14)), [13, 20, 21], list(range(13)) + [20, 21], 0, 0),  # two B-only output bits on top
+    (list(range(14)), [13, 20, 21], [21] + list(range(13)) + [20], 1, 1),  # B-only bits at 0 and top, shifted
+    ([5, 0, 3, 1, 2, 4, 6, 7, 8, 9, 10, 11], [4, 30], [30, 0, 1, 2, 3] + list(range(5, 12)), 0, 0),  # scattered A
 ]
 
 
