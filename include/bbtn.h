@@ -193,7 +193,15 @@ typedef struct {
     int branch_lookahead;    /* seed of each branching region: the variable, among the this-many
                                 carrying the most overflow, whose branching has the smallest
                                 gamma (default 1: the one carrying the most overflow) */
-    int reserved[5];
+    int leaf_trials;         /* BBTN counting leaves: order-finder trials (host threads) for each
+                                leaf's own contraction order, used when it fits the cap with less
+                                work than the root order restricted to the leaf (default 8; 0 =
+                                always the root order) */
+    int autotune;            /* time the register-tiled kernel's four load layouts on the first
+                                step of each shape class and keep the fastest for the context's
+                                later solves (default 0: the bit-0 rule, which the tuned choice
+                                matched on the 30x30 King's-subgraph workload) */
+    int reserved[3];
 } bbtn_opts;
 
 typedef struct {
@@ -223,10 +231,15 @@ typedef struct {
     double prof_stream_ms;   /* streaming gather kernel (K1/K3): device time, bytes, launches */
     double prof_stream_bytes;
     int64_t prof_stream_launches;
-    double prof_tiled_ms;    /* register-tiled kernel (K1t): device time, multiply-adds, launches */
+    double prof_tiled_ms;    /* register-tiled kernel (K1t), value-only steps: device time,
+                                multiply-adds, launches */
     double prof_tiled_ops;
     int64_t prof_tiled_launches;
-    int reserved[8];
+    int64_t prof_tiled16_launches; /* of those, launches with two 16-bit lanes per instruction */
+    double prof_tcount_ms;   /* register-tiled kernel (K1t), counting steps: device time,
+                                multiply-adds, launches */
+    double prof_tcount_ops;
+    int64_t prof_tcount_launches;
 } bbtn_stats;
 
 /* Fill *opts with defaults. */

@@ -156,7 +156,8 @@ class Solver:
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
-                 profile: bool = False, branch_lookahead: int = 1, stream=None, workspace=None):
+                 profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 8, autotune: bool = False,
+                 stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
@@ -164,6 +165,7 @@ class Solver:
         o.sa_iters, o.region_size, o.batch, o.use_gnn = sa_iters, region_size, batch, int(use_gnn)
         o.count_check, o.use_symmetry = count_check, int(use_symmetry)
         o.max_slices_log2, o.profile, o.branch_lookahead = max_slices_log2, int(profile), branch_lookahead
+        o.leaf_trials, o.autotune = leaf_trials, int(autotune)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:

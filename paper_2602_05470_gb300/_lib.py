@@ -30,7 +30,8 @@ class Opts(C.Structure):
                 ("mode", C.c_int), ("sa_iters", C.c_int), ("region_size", C.c_int),
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
-                ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("reserved", C.c_int * 5)]
+                ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("leaf_trials", C.c_int),
+                ("autotune", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class Stats(C.Structure):
@@ -44,7 +45,8 @@ class Stats(C.Structure):
                 ("prof_big_launches", C.c_int64), ("prof_stream_ms", C.c_double),
                 ("prof_stream_bytes", C.c_double), ("prof_stream_launches", C.c_int64),
                 ("prof_tiled_ms", C.c_double), ("prof_tiled_ops", C.c_double), ("prof_tiled_launches", C.c_int64),
-                ("reserved", C.c_int * 8)]
+                ("prof_tiled16_launches", C.c_int64), ("prof_tcount_ms", C.c_double),
+                ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}

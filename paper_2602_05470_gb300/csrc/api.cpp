@@ -25,6 +25,7 @@ struct bbtn_ctx {
     SolveOutput out;
     bbtn_stats stats;
     Arena arena;
+    TileTuner tuner;                   // tuned load layouts, kept across solves
     GnnModel *gnn_branch = nullptr;   // borrowed (bbtn_set_gnn)
     GnnModel *gnn_value = nullptr;
 };
@@ -281,6 +282,8 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->profile = 0;
     o->max_slices_log2 = 30;
     o->branch_lookahead = 1;
+    o->leaf_trials = 8;
+    o->autotune = 0;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -297,6 +300,7 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
         if (o.batch < 1) fail(BBTN_EINVAL, "batch < 1");
         if (o.sa_iters < 0) fail(BBTN_EINVAL, "sa_iters < 0");
         if (o.branch_lookahead < 0 || o.branch_lookahead > 1024) fail(BBTN_EINVAL, "branch_lookahead outside 0..1024");
+        if (o.leaf_trials < 0 || o.leaf_trials > 256) fail(BBTN_EINVAL, "leaf_trials outside 0..256");
         // without a usable device the context still plans on the host (bbtn_analyze);
         // every call that needs the device then fails with BBTN_ECUDA
         if (cudaGetDevice(&ctx->device) == cudaSuccess &&
@@ -398,7 +402,7 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         ctx->solved = false;
         if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
         BBTN_CUDA(cudaSetDevice(ctx->device));
-        Solver s(ctx->opts, ctx->stream, &ctx->arena);
+        Solver s(ctx->opts, ctx->stream, &ctx->arena, &ctx->tuner);
         s.set_gnn(ctx->gnn_branch, ctx->gnn_value);
         ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
         ctx->solved = true;

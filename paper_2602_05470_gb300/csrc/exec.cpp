@@ -127,7 +127,9 @@ void Profiler::collect() {
         ops += r.ops;
         launches++;
         if (r.kind == 0 || r.kind == 3) { stream_ms += t; stream_bytes += r.bytes; stream_launches++; }
-        if (r.kind == 2) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
+        if (r.kind == 2 || r.kind == 4) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
+        if (r.kind == 4) tiled16_launches++;
+        if (r.kind == 5) { tcount_ms += t; tcount_ops += r.ops; tcount_launches++; }
         if (r.bytes >= kBig) {
             big_ms += t;
             big_bytes += r.bytes;
@@ -550,6 +552,7 @@ struct LaunchTimer {
     }
     void done(double bytes, double ops, const ContractParams *P, int kind, int n) {
         if (!pr) return;
+        if (kind == 2 && P) kind = P->np > 0 ? 5 : (P->v16 ? 4 : 2);
         BBTN_CUDA(cudaEventRecord(b, s));
         int ra = 0, rb = 0, ident = 0, rc = 0, rs = 0;
         if (P) {
@@ -563,7 +566,66 @@ struct LaunchTimer {
     }
 };
 
+// Shape class of a tiled step: the group sizes (batch, m, n, k) and the role
+// (free in one operand, batch, summed, absent) of each operand's two lowest bits --
+// what decides how its loads coalesce. Leaves of one tree give the same few classes.
+uint64_t step_signature(const ContractParams &P) {
+    int nb = 0, nm = 0, nn = 0;
+    for (int i = 0; i < P.rc; i++) {
+        if (P.oA[i] >= 0 && P.oB[i] >= 0) nb++;
+        else if (P.oA[i] >= 0) nm++;
+        else nn++;
+    }
+    auto role = [&](const int8_t *o, const int8_t *other, const int8_t *sm, int q) {
+        for (int i = 0; i < P.rc; i++)
+            if (o[i] == q) return other[i] >= 0 ? 2 : 1;   // batch / free
+        for (int j = 0; j < P.rs; j++)
+            if (sm[j] == q) return 3;                       // summed
+        return 0;
+    };
+    uint64_t h = (uint64_t)P.np | (uint64_t)P.v16 << 4 | (uint64_t)nb << 8 | (uint64_t)nm << 16 |
+                 (uint64_t)nn << 24 | (uint64_t)P.rs << 32;
+    h |= (uint64_t)role(P.oA, P.oB, P.sA, 0) << 40 | (uint64_t)role(P.oA, P.oB, P.sA, 1) << 42;
+    h |= (uint64_t)role(P.oB, P.oA, P.sB, 0) << 44 | (uint64_t)role(P.oB, P.oA, P.sB, 1) << 46;
+    return h;
+}
+
 }  // namespace
+
+int TileTuner::pick(uint64_t key, const std::function<cudaError_t(int)> &launch, cudaStream_t s) {
+    auto it = best.find(key);
+    if (it != best.end()) return it->second;
+    if (!ev[0]) {
+        BBTN_CUDA(cudaEventCreate(&ev[0]));
+        BBTN_CUDA(cudaEventCreate(&ev[1]));
+    }
+    // two rounds in opposite orders, each candidate's faster time counts: the first
+    // launch finds the operands outside L2, so a single round favours the later ones
+    float t[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+    for (int round = 0; round < 2; round++)
+        for (int i = 0; i < 4; i++) {
+            const int l = round ? 3 - i : i;
+            BBTN_CUDA(cudaEventRecord(ev[0], s));
+            cudaError_t e = launch(l);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("tiled (tuning): ") + cudaGetErrorString(e));
+            BBTN_CUDA(cudaEventRecord(ev[1], s));
+            BBTN_CUDA(cudaEventSynchronize(ev[1]));
+            float ms = 0;
+            BBTN_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+            t[l] = std::min(t[l], ms);
+        }
+    int choice = 0;
+    for (int l = 1; l < 4; l++)
+        if (t[l] < t[choice]) choice = l;
+    best[key] = choice;
+    tuned++;
+    return choice;
+}
+
+TileTuner::~TileTuner() {
+    for (auto e : ev)
+        if (e) cudaEventDestroy(e);
+}
 
 void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net, char *arena, uint64_t stride,
                int32_t *out_val, uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st,
@@ -649,7 +711,7 @@ void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net,
                 P.planeC = 1ull << P.rc;
             }
             void *scratch = pl.splitk_bytes ? ar + pl.splitk_off : nullptr;
-            if (nl > 1 && !(scratch && splitk_eligible(P))) {
+            if (!(scratch && splitk_eligible(P))) {
                 if (tiled_eligible(P)) {
                     tiled.push_back(P);
                     t_bytes += ps.bytes;
@@ -671,8 +733,12 @@ void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net,
             if (st) st->launches++;
         }
         if (!tiled.empty()) {
+            int lanes = -1;
+            if (st && st->tuner)   // timed on the first leaf's step alone
+                lanes = st->tuner->pick(step_signature(tiled[0]),
+                                        [&](int l) { return launch_contract_tiled_batch(tiled.data(), 1, s, l); }, s);
             LaunchTimer lt(pr, s);
-            cudaError_t e = launch_contract_tiled_batch(tiled.data(), (int)tiled.size(), s);
+            cudaError_t e = launch_contract_tiled_batch(tiled.data(), (int)tiled.size(), s, lanes);
             if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("tiled batch: ") + cudaGetErrorString(e));
             lt.done(t_bytes, t_ops, &tiled[0], 2, (int)tiled.size());
             if (st) st->launches++;

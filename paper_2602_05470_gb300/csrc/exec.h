@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.h"
@@ -87,17 +89,32 @@ struct Profiler {
     size_t used = 0;
     double ms = 0, bytes = 0, ops = 0, big_ms = 0, big_bytes = 0;
     int64_t launches = 0, big_launches = 0;
-    double stream_ms = 0, stream_bytes = 0, tiled_ms = 0, tiled_ops = 0;   // per kernel
-    int64_t stream_launches = 0, tiled_launches = 0;
+    // per kernel; kind: 0 streaming, 1 fused, 2 tiled value-only (int32), 3 split-K,
+    // 4 tiled value-only (16-bit lanes), 5 tiled counting
+    double stream_ms = 0, stream_bytes = 0, tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0;
+    int64_t stream_launches = 0, tiled_launches = 0, tiled16_launches = 0, tcount_launches = 0;
     cudaEvent_t get();
     void collect();          // after the stream has been synchronised
     ~Profiler();
+};
+
+// Autotuner of the tiled kernel's load layout (which operand dimension its lanes
+// run along, for A and for B): the first launch of a step signature times all four
+// choices on the real step (each writes the same result) and keeps the fastest
+// for every later launch with that signature.
+struct TileTuner {
+    std::unordered_map<uint64_t, int> best;   // signature -> lanes (0..3)
+    int64_t tuned = 0;                        // signatures timed so far
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int pick(uint64_t key, const std::function<cudaError_t(int)> &launch, cudaStream_t s);
+    ~TileTuner();
 };
 
 struct RunStats {
     int64_t launches = 0;
     double ops = 0, bytes = 0;
     Profiler *prof = nullptr;
+    TileTuner *tuner = nullptr;
 };
 
 // Grow-only device buffer for the fused-subtree programs.

@@ -59,7 +59,9 @@ bool stream4_eligible(const ContractParams &p);
 // (all entries: same np and hasB). cudaErrorNotSupported if an entry does not fit.
 constexpr int kBatchMax = 16;
 cudaError_t launch_contract_stream4_batch(const ContractParams *p, int n, cudaStream_t s);
-cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s);
+// lanes: -1 = lanes along k for an operand whose bit 0 is a summed label, else along
+// m / n; 0..3 = forced (bit 0: A along k, bit 1: B along k), as an autotuner picks it
+cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s, int lanes = -1);
 bool tiled_eligible(const ContractParams &p);
 
 // out bit q <- in bit perm[q]

@@ -444,7 +444,9 @@ void Solver::setup_host(const Problem &p, bool want_count) {
 // counting-sum in slot 0 (paper: the result is the sum over the branches);
 // without, only the leaves' maxima are computed (value planes only). Returns the
 // leaves' values.
-std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting) {
+std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting,
+                                             const CTree *tree) {
+    const CTree &tr = tree ? *tree : tree_;
     if (leaves.empty()) return {};
     const int64_t n = (int64_t)leaves.size();
     ensure_buffers(n + 1);   // slots 0..n, temporary at dcap_ > n
@@ -455,6 +457,7 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
     BBTN_CUDA(cudaEventRecord(e0, stream_));
     const double tw = now_s();
     RunStats rs;
+    rs.tuner = opts_.autotune ? tuner_ : nullptr;
     rs.prof = opts_.profile ? &prof_ : nullptr;
     if (rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
         prof_.dump = fopen(getenv("BBTN_PROFILE_DUMP"), "w");
@@ -464,7 +467,7 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
     // leaf i of a group gets its own arena at i * stride
     const double tp = now_s();
     std::vector<Plan> plans(n);
-    parallel_for(n, [&](int64_t i) { plans[i] = make_plan(tree_, net_, leaves[i], counting ? np_ : 0, cprime_, false); });
+    parallel_for(n, [&](int64_t i) { plans[i] = make_plan(tr, net_, leaves[i], counting ? np_ : 0, cprime_, false); });
     st_->t_plan_s += now_s() - tp;
     uint64_t stride = 256;
     for (const Plan &pl : plans) {
@@ -516,6 +519,10 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
         st_->prof_tiled_ms = prof_.tiled_ms;
         st_->prof_tiled_ops = prof_.tiled_ops;
         st_->prof_tiled_launches = prof_.tiled_launches;
+        st_->prof_tiled16_launches = prof_.tiled16_launches;
+        st_->prof_tcount_ms = prof_.tcount_ms;
+        st_->prof_tcount_ops = prof_.tcount_ops;
+        st_->prof_tcount_launches = prof_.tcount_launches;
     }
     st_->kernel_ms += ms;
     st_->t_device_s += now_s() - tw;
@@ -811,11 +818,50 @@ void Solver::search(bool dry, BranchLog *log) {
         for (size_t i = 0; i < cand.size(); i++)
             if (cand_val[i] == incumbent_) opt.push_back(std::move(cand[i]));
         st_->pruned += (int64_t)(cand.size() - opt.size());
-        for (size_t i = 0; i < opt.size(); i += (size_t)bs) {
-            std::vector<std::vector<int8_t>> b(opt.begin() + i, opt.begin() + std::min(opt.size(), i + (size_t)bs));
+        // counting leaves with an order of their own run alone; the others in batches
+        std::vector<std::vector<int8_t>> rest;
+        for (auto &fx : opt) {
+            CTree t;
+            const double tp = now_s();
+            const bool own = leaf_order(fx, t);
+            st_->t_plan_s += now_s() - tp;
+            if (own) contract_leaves({fx}, true, &t);
+            else rest.push_back(std::move(fx));
+        }
+        for (size_t i = 0; i < rest.size(); i += (size_t)bs) {
+            std::vector<std::vector<int8_t>> b(rest.begin() + i, rest.begin() + std::min(rest.size(), i + (size_t)bs));
             contract_leaves(b, true);
         }
     }
+}
+
+// A contraction order for one leaf sub-network of its own: opts.leaf_trials greedy +
+// annealing runs on the leaf's free variables (one per host thread, different
+// seeds). True, with the order in `out`, when the best of them fits the space cap
+// with fewer multiply-adds than the root order restricted to the leaf (every
+// ordering gives the same contraction value, paper Eq. (2)).
+bool Solver::leaf_order(const std::vector<int8_t> &fx, CTree &out) {
+    const int trials = opts_.leaf_trials;
+    if (trials <= 0) return false;
+    const int cap = opts_.space_cap_log2;
+    std::vector<char> rem(p_->n, 0);
+    for (int v = 0; v < p_->n; v++) rem[v] = fx[v] >= 0;
+    const Cost ref = tree_cost(tree_, cap, &rem);
+    std::vector<std::vector<int>> ll(net_.labels.size());
+    for (size_t i = 0; i < ll.size(); i++)
+        for (int l : net_.labels[i]) if (fx[l] < 0) ll[i].push_back(l);
+    std::vector<CTree> cand(trials);
+    std::vector<Cost> cost(trials);
+    parallel_for(trials, [&](int64_t t) {
+        cand[t] = find_order(ll, p_->n, cap, 1.0, 1, opts_.sa_iters, opts_.seed * 131 + 17 + (uint64_t)t);
+        cost[t] = tree_cost(cand[t], cap);
+    });
+    int best = -1;
+    for (int t = 0; t < trials; t++)
+        if (cost[t].sc <= cap && cost[t].tc_log2 < (best < 0 ? ref.tc_log2 : cost[best].tc_log2)) best = t;
+    if (best < 0) return false;
+    out = std::move(cand[best]);
+    return true;
 }
 
 void Solver::finish(bool want_config) {
@@ -839,6 +885,7 @@ void Solver::finish(bool want_config) {
         arena_->reserve(plan.arena_bytes);
         int32_t *root = d_val_ + dcap_;
         RunStats rs;
+        rs.tuner = opts_.autotune ? tuner_ : nullptr;
         run_plan(plan, net_, arena_->ptr, root, nullptr, 0, stream_, &rs, &prog_);
         backward_config(plan, tree_, net_, arena_->ptr, root, best_fx_, out_.x, stream_);
         st_->launches += rs.launches + (int64_t)plan.steps.size();

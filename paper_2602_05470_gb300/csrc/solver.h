@@ -37,7 +37,8 @@ struct BranchLog {
 
 class Solver {
   public:
-    Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena) : opts_(o), stream_(s), arena_(arena) {}
+    Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena, TileTuner *tuner = nullptr)
+        : opts_(o), stream_(s), arena_(arena), tuner_(tuner) {}
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
     // host-only planning summary (bbtn_analyze)
     void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);
@@ -55,7 +56,9 @@ class Solver {
     struct Leafset;
     void setup(const Problem &p, bool want_count);
     void setup_host(const Problem &p, bool want_count);
-    std::vector<int32_t> contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting = true);
+    std::vector<int32_t> contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting = true,
+                                         const CTree *tree = nullptr);
+    bool leaf_order(const std::vector<int8_t> &fx, CTree &out);
     void finish(bool want_config);
     void run_plain();
     void run_sliced();
@@ -92,6 +95,7 @@ class Solver {
     bbtn_stats *st_ = nullptr;
     SolveOutput out_;
     Profiler prof_;
+    TileTuner *tuner_ = nullptr;        // borrowed from the context (kept across solves)
     DeviceBuf prog_;                    // fused-subtree programs
     GnnModel *gnn_ = nullptr;
     GnnModel *gnn_branch_ = nullptr;

@@ -441,14 +441,19 @@ cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
     return dispatch_t<1>(&p, &g, &fa, &fb, 1, s);
 }
 
-cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s) {
+cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s, int lanes) {
     if (n <= 0) return cudaSuccess;
-    if (n > kBatchMax) return cudaErrorInvalidValue;
+    if (n > kBatchMax || lanes < -1 || lanes > 3) return cudaErrorInvalidValue;
     Groups g[kBatchMax];
     int fa[kBatchMax], fb[kBatchMax];
-    for (int i = 0; i < n; i++)
+    for (int i = 0; i < n; i++) {
         if (p[i].np != p[0].np || p[i].v16 != p[0].v16 || !make_groups(p[i], g[i], fa[i], fb[i]))
             return cudaErrorNotSupported;
+        if (lanes >= 0) {   // the caller's (an autotuner's) choice instead of the bit-0 rule
+            fa[i] = lanes & 1;
+            fb[i] = (lanes >> 1) & 1;
+        }
+    }
     if (n == 1) return dispatch_t<1>(p, g, fa, fb, 1, s);
     return dispatch_t<kBatchMax>(p, g, fa, fb, n, s);
 }

@@ -146,3 +146,18 @@ def test_ksg_30x30_bbtn_sample(P):
         inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
         res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24).solve(inst, count=True, config=True)
         _check(inst, res, row["alpha"], int(row["count"]))
+
+
+def test_ksg_30x30_options_do_not_change_the_answer(P):
+    """The autotuner (timed load layouts of the tiled kernel), the per-leaf orders
+    of the counting leaves and the leaf batching only change how the contraction
+    runs: with all of them off the third workload instance gives the stored
+    oracle answer too, and so does a second solve that reuses tuned layouts."""
+    with open(GOLDEN) as f:
+        row = json.load(f)["ksg_30x30_f2"][2]
+    inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+    plain = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, autotune=False, leaf_trials=0, batch=1)
+    _check(inst, plain.solve(inst, count=True, config=True), row["alpha"], int(row["count"]))
+    tuned = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, autotune=True)
+    for _ in range(2):
+        _check(inst, tuned.solve(inst, count=True, config=False), row["alpha"], int(row["count"]))
