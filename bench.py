@@ -41,6 +41,26 @@ def instances(rank: int, world: int, step: int, per_step: int):
     return out
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "launch_list_ksg30x30_bbtn.md")
+TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, instance 0 of this workload "
+                  "(profiles/launch_list_ksg30x30_bbtn.md)")
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of each kernel from the committed ncu summary of this
+    workload (its table rows read '| `kernel` (...) | launches | read + write | N MB |')."""
+    out = {}
+    try:
+        import re
+        for line in open(TRAFFIC_FILE):
+            m = re.match(r"\|\s*`([^`]+)`.*\|\s*([\d.]+)\s*MB\s*\|\s*$", line)
+            if m:
+                out[m.group(1)] = float(m.group(2)) * 1e6
+    except OSError:
+        pass
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -214,8 +234,9 @@ def run_ours(args, rank, world, local_rank):
     # roofline: one more pass over step 0's instances with every contraction launch
     # bracketed by CUDA events on this stream (not part of the timed region)
     keys = ("prof_ms", "prof_bytes", "prof_ops", "prof_launches", "prof_stream_ms", "prof_stream_bytes",
-            "prof_stream_launches", "prof_tiled_ms", "prof_tiled_ops", "prof_tiled_launches",
-            "prof_tiled16_launches", "prof_tcount_ms", "prof_tcount_ops", "prof_tcount_launches")
+            "prof_stream_launches", "prof_scount_ms", "prof_scount_bytes", "prof_scount_launches",
+            "prof_tiled_ms", "prof_tiled_ops", "prof_tiled_launches", "prof_tiled16_launches", "prof_tcount_ms",
+            "prof_tcount_ops", "prof_tcount_launches")
     pb = {k: 0.0 for k in keys}
     if not args.no_profile_pass:
         prof = make_solver(profile=True)
@@ -224,24 +245,33 @@ def run_ours(args, rank, world, local_rank):
             for k in pb:
                 pb[k] += r.stats[k]
     peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic()
 
-    def entry(kernel, bound, ms, work, launches, pk, unit, source, scale):
+    def entry(kernel, ncu_name, bound, ms, work, launches, pk, unit, source, scale):
         ach = work / (ms * scale) if ms else 0.0
         return {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
-                "traffic": None, "kernel": kernel, "launches": int(launches),
-                "avg_launch_us": 1000 * ms / max(launches, 1), "device_ms": ms, "peak_source": source}
+                "traffic": traffic.get(ncu_name), "traffic_source": TRAFFIC_SOURCE if ncu_name in traffic else None,
+                "algorithmic_bytes_per_launch": (pb_bytes.get(ncu_name, 0.0) / max(launches, 1)) or None,
+                "kernel": kernel, "launches": int(launches), "avg_launch_us": 1000 * ms / max(launches, 1),
+                "device_ms": ms, "peak_source": source}
 
+    pb_bytes = {"k_contract4<0, 1, 16>": pb["prof_stream_bytes"], "k_contract4<4, 1, 1>": pb["prof_scount_bytes"]}
     all16 = pb["prof_tiled_launches"] > 0 and pb["prof_tiled16_launches"] == pb["prof_tiled_launches"]
+    alu_src = "derived: 152 SMs x 64 ALU lanes x 2.07 GHz, one add+max instruction per op"
     kernels = [
-        entry("k_contract4 (streaming gather, K1v; value-only and counting steps)", "hbm", pb["prof_stream_ms"],
-              pb["prof_stream_bytes"], pb["prof_stream_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6),
+        entry("k_contract4 value-only (streaming gather, K1v)", "k_contract4<0, 1, 16>", "hbm",
+              pb["prof_stream_ms"], pb["prof_stream_bytes"], pb["prof_stream_launches"], peak, "GB/s",
+              peak_kind + " HBM copy", 1e6),
+        entry("k_contract4 counting (streaming gather, K1v, 4 residue planes)", "k_contract4<4, 1, 1>", "hbm",
+              pb["prof_scount_ms"], pb["prof_scount_bytes"], pb["prof_scount_launches"], peak, "GB/s",
+              peak_kind + " HBM copy", 1e6),
         entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
-              "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"], pb["prof_tiled_launches"],
-              ALU_PEAK_TOPS * (2 if all16 else 1), "T tropical ops/s",
-              "derived: 152 SMs x 64 ALU lanes x 2.07 GHz" + (" x 2 lanes" if all16 else ""), 1e9),
-        entry("k_tiled counting (register-tiled, K1t, 4 residue planes)", "alu", pb["prof_tcount_ms"],
-              pb["prof_tcount_ops"], pb["prof_tcount_launches"], ALU_PEAK_TOPS, "T tropical ops/s",
-              "derived: 152 SMs x 64 ALU lanes x 2.07 GHz (add+max only; ties add modular products)", 1e9),
+              "k_tiled<0, 16, 1>" if all16 else "k_tiled<0, 16, 0>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
+              pb["prof_tiled_launches"], ALU_PEAK_TOPS * (2 if all16 else 1), "T tropical ops/s",
+              alu_src + (" x 2 lanes" if all16 else ""), 1e9),
+        entry("k_tiled counting (register-tiled, K1t, 4 residue planes)", "k_tiled<4, 1, 0>", "alu",
+              pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], ALU_PEAK_TOPS,
+              "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
     ]
     order = sorted(range(len(kernels)), key=lambda i: -kernels[i]["device_ms"])
     dominant = dict(kernels[order[0]])

@@ -225,10 +225,11 @@ typedef struct {
     double prof_bytes;       /* their algorithmic bytes */
     double prof_ops;         /* their multiply-adds */
     int64_t prof_launches;
-    double prof_big_ms;      /* the same for launches moving >= 64 MiB */
-    double prof_big_bytes;
-    int64_t prof_big_launches;
-    double prof_stream_ms;   /* streaming gather kernel (K1/K3): device time, bytes, launches */
+    double prof_scount_ms;   /* streaming gather kernel, counting steps: device time, bytes, launches */
+    double prof_scount_bytes;
+    int64_t prof_scount_launches;
+    double prof_stream_ms;   /* streaming gather kernel (K1/K3), value-only steps: device time,
+                                bytes, launches */
     double prof_stream_bytes;
     int64_t prof_stream_launches;
     double prof_tiled_ms;    /* register-tiled kernel (K1t), value-only steps: device time,

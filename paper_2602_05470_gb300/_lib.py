@@ -41,8 +41,8 @@ class Stats(C.Structure):
                 ("launches", C.c_int64), ("steps", C.c_int64), ("sc_log2", C.c_int),
                 ("tc_log2", C.c_double), ("sc_plain_log2", C.c_double), ("slices_log2", C.c_int),
                 ("prof_ms", C.c_double), ("prof_bytes", C.c_double), ("prof_ops", C.c_double),
-                ("prof_launches", C.c_int64), ("prof_big_ms", C.c_double), ("prof_big_bytes", C.c_double),
-                ("prof_big_launches", C.c_int64), ("prof_stream_ms", C.c_double),
+                ("prof_launches", C.c_int64), ("prof_scount_ms", C.c_double), ("prof_scount_bytes", C.c_double),
+                ("prof_scount_launches", C.c_int64), ("prof_stream_ms", C.c_double),
                 ("prof_stream_bytes", C.c_double), ("prof_stream_launches", C.c_int64),
                 ("prof_tiled_ms", C.c_double), ("prof_tiled_ops", C.c_double), ("prof_tiled_launches", C.c_int64),
                 ("prof_tiled16_launches", C.c_int64), ("prof_tcount_ms", C.c_double),

@@ -115,7 +115,6 @@ cudaEvent_t Profiler::get() {
 }
 
 void Profiler::collect() {
-    constexpr double kBig = 64.0 * 1024 * 1024;
     for (const Rec &r : recs) {
         float t = 0;
         BBTN_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
@@ -127,14 +126,10 @@ void Profiler::collect() {
         ops += r.ops;
         launches++;
         if (r.kind == 0 || r.kind == 3) { stream_ms += t; stream_bytes += r.bytes; stream_launches++; }
+        if (r.kind == 6) { scount_ms += t; scount_bytes += r.bytes; scount_launches++; }
         if (r.kind == 2 || r.kind == 4) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
         if (r.kind == 4) tiled16_launches++;
         if (r.kind == 5) { tcount_ms += t; tcount_ops += r.ops; tcount_launches++; }
-        if (r.bytes >= kBig) {
-            big_ms += t;
-            big_bytes += r.bytes;
-            big_launches++;
-        }
     }
     recs.clear();
     used = 0;
@@ -553,6 +548,7 @@ struct LaunchTimer {
     void done(double bytes, double ops, const ContractParams *P, int kind, int n) {
         if (!pr) return;
         if (kind == 2 && P) kind = P->np > 0 ? 5 : (P->v16 ? 4 : 2);
+        if ((kind == 0 || kind == 3) && P && P->np > 0) kind = 6;
         BBTN_CUDA(cudaEventRecord(b, s));
         int ra = 0, rb = 0, ident = 0, rc = 0, rs = 0;
         if (P) {

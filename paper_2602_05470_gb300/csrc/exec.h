@@ -87,12 +87,13 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> recs;
     size_t used = 0;
-    double ms = 0, bytes = 0, ops = 0, big_ms = 0, big_bytes = 0;
-    int64_t launches = 0, big_launches = 0;
-    // per kernel; kind: 0 streaming, 1 fused, 2 tiled value-only (int32), 3 split-K,
-    // 4 tiled value-only (16-bit lanes), 5 tiled counting
-    double stream_ms = 0, stream_bytes = 0, tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0;
-    int64_t stream_launches = 0, tiled_launches = 0, tiled16_launches = 0, tcount_launches = 0;
+    double ms = 0, bytes = 0, ops = 0;
+    int64_t launches = 0;
+    // per kernel; kind: 0 streaming value-only, 1 fused, 2 tiled value-only (int32),
+    // 3 split-K, 4 tiled value-only (16-bit lanes), 5 tiled counting, 6 streaming counting
+    double stream_ms = 0, stream_bytes = 0, scount_ms = 0, scount_bytes = 0;
+    double tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0;
+    int64_t stream_launches = 0, scount_launches = 0, tiled_launches = 0, tiled16_launches = 0, tcount_launches = 0;
     cudaEvent_t get();
     void collect();          // after the stream has been synchronised
     ~Profiler();

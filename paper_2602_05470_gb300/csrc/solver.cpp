@@ -510,9 +510,9 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
         st_->prof_bytes = prof_.bytes;
         st_->prof_ops = prof_.ops;
         st_->prof_launches = prof_.launches;
-        st_->prof_big_ms = prof_.big_ms;
-        st_->prof_big_bytes = prof_.big_bytes;
-        st_->prof_big_launches = prof_.big_launches;
+        st_->prof_scount_ms = prof_.scount_ms;
+        st_->prof_scount_bytes = prof_.scount_bytes;
+        st_->prof_scount_launches = prof_.scount_launches;
         st_->prof_stream_ms = prof_.stream_ms;
         st_->prof_stream_bytes = prof_.stream_bytes;
         st_->prof_stream_launches = prof_.stream_launches;
