@@ -11,7 +11,7 @@ namespace bbtn {
 constexpr int kGnnFeat = 8;     // input features per vertex
 constexpr int kGnnHidden = 64;  // hidden width
 constexpr int kGnnLayers = 3;
-constexpr int kGnnBranchCandidates = 16;   // seeds a branch scorer chooses among (at least)
+constexpr int kGnnBranchCandidates = 8;    // seeds a branch scorer chooses among (at least)
 
 cudaError_t gnn_gather(int n, int d, const int *rowp, const int *col, const float *H, float *M, cudaStream_t s);
 cudaError_t gnn_dense(int n, int din, int dout, const float *X, const float *M, const float *W, const float *U,

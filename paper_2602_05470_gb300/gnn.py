@@ -163,7 +163,7 @@ def mean_loss(model: GNN, data) -> float:
 
 # ---------------------------------------------------------------- branch scorer data
 
-def branch_rows(inst, cap: int, max_rows: int, lookahead: int = 16, seed: int = 1):
+def branch_rows(inst, cap: int, max_rows: int, lookahead: int = 16, seed: int = 1, region_size: int = 8):
     """Training rows of the branch scorer from one instance (host-side search).
 
     Every expanded node of the lookahead search gives one row: features with the
@@ -172,7 +172,7 @@ def branch_rows(inst, cap: int, max_rows: int, lookahead: int = 16, seed: int = 
     signal and are dropped.
     """
     from . import Solver
-    s = Solver(space_cap_log2=cap, seed=seed)
+    s = Solver(space_cap_log2=cap, seed=seed, region_size=region_size)
     fx, sc, ga = s.branch_samples(inst, max_rows, lookahead)
     s.close()
     out = []
@@ -190,14 +190,16 @@ def branch_rows(inst, cap: int, max_rows: int, lookahead: int = 16, seed: int = 
 
 
 def _rows_job(args):
-    kind, N, seed, cap, max_rows, lookahead = args
+    kind, N, seed, cap, max_rows, lookahead = args[:6]
+    region_size = args[6] if len(args) > 6 else 8
     import synth
     inst = synth.kings_subgraph(N, 0.8, seed=seed)
-    return inst, branch_rows(inst, cap, max_rows, lookahead)
+    return inst, branch_rows(inst, cap, max_rows, lookahead, region_size=region_size)
 
 
 def branch_dataset(specs, workers: int = 0):
-    """[(kind, N, seed, cap, max_rows, lookahead)] -> [(inst, rows)], host processes in parallel."""
+    """[(kind, N, seed, cap, max_rows, lookahead[, region_size])] -> [(inst, rows)], host
+    processes in parallel."""
     import multiprocessing as mp
     import os
     workers = workers or max(1, (os.cpu_count() or 2) - 1)
