@@ -31,14 +31,26 @@ METRIC = "time-to-exact-count per instance (KSG 30x30 MIS, BBTN)"
 WORKLOAD = "mis_kings_subgraph_30x30_filling0.8_cap2^24_bbtn_counting"
 
 
+def shard_indices(rank: int, world: int, step: int, per_step: int):
+    """Workload instances of one rank in one step: the ranks of a step take
+    consecutive, disjoint blocks of per_step instances (weak scaling)."""
+    return [(step * per_step * world + rank * per_step + j) % N_INST for j in range(per_step)]
+
+
 def instances(rank: int, world: int, step: int, per_step: int):
     import synth
-    out = []
-    for j in range(per_step):
-        idx = (step * per_step * world + rank * per_step + j) % N_INST
-        seed = synth.config_seed(2, idx)
-        out.append((idx, synth.kings_subgraph(N_GRID, FILLING, seed=seed)))
-    return out
+    return [(idx, synth.kings_subgraph(N_GRID, FILLING, seed=synth.config_seed(2, idx)))
+            for idx in shard_indices(rank, world, step, per_step)]
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "launch_list_ksg30x30_bbtn.md")
@@ -226,10 +238,7 @@ def run_ours(args, rank, world, local_rank):
         for k, v in st.items():
             stats[k] = stats.get(k, 0) + v
     ck = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
-    if dist:
-        t = torch.tensor([tot_dev, tot_wall], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_dev, tot_wall = float(t[0]), float(t[1])
+    tot_dev, tot_wall = max_over_ranks([tot_dev, tot_wall], dist, "cuda")
     n_inst = per * args.steps * world
     # roofline: one more pass over step 0's instances with every contraction launch
     # bracketed by CUDA events on this stream (not part of the timed region)
@@ -307,13 +316,13 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": tot_dev / (per * args.steps), "unit": "s/instance",
+        "metric": METRIC, "value": tot_dev / n_inst, "unit": "s/instance",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot_dev / args.steps, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32+u64(mod 2^61-c)", "data": "synthetic (seeded King's subgraphs)",
         "config": {"workload": WORKLOAD, "instances_per_step": per, "instances_total": n_inst,
                    "space_cap_log2": CAP, "n_primes": 3, "l2": "256 MiB flush between steps; tensors up to 470 MB"},
-        "e2e": {"value": tot_wall / (per * args.steps), "unit": "s/instance",
+        "e2e": {"value": tot_wall / n_inst, "unit": "s/instance",
                 "h2d_bytes_per_step": H2D // args.steps, "d2h_bytes_per_step": D2H // args.steps},
         "gpu_launches": int(stats.get("launches", 0)),
         "tropical_gops": stats.get("tropical_ops", 0) / tot_dev / 1e9 if tot_dev else 0.0,
