@@ -2,6 +2,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <exception>
+#include <thread>
 #include <limits>
 #include <queue>
 #include <unordered_set>
@@ -304,9 +306,12 @@ void tree_sa(CTree &t, const SAParams &sp, uint64_t seed) {
 
 CTree find_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, int cap, double w_rho,
                  int trials, int sa_beta_steps, uint64_t seed) {
-    CTree best;
-    double best_f = std::numeric_limits<double>::infinity();
-    for (int tr = 0; tr < std::max(1, trials); tr++) {
+    // independent restarts, one host thread each; the best objective wins (ties:
+    // the lowest trial index, so the result does not depend on thread timing)
+    const int nt = std::max(1, trials);
+    std::vector<CTree> trees(nt);
+    std::vector<double> f(nt, std::numeric_limits<double>::infinity());
+    auto run = [&](int tr) {
         CTree t = greedy_order(leaf_labels, nvars, seed * 7919 + tr, tr == 0 ? 0.0 : 0.3);
         if (sa_beta_steps > 0) {
             SAParams sp;
@@ -316,10 +321,30 @@ CTree find_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, in
             tree_sa(t, sp, seed * 104729 + tr);
         }
         Cost c = tree_cost(t, cap);
-        double f = c.tc_log2 + w_rho * c.rho;
-        if (f < best_f) { best_f = f; best = std::move(t); }
+        f[tr] = c.tc_log2 + w_rho * c.rho;
+        trees[tr] = std::move(t);
+    };
+    if (nt == 1) {
+        run(0);
+    } else {
+        std::vector<std::thread> th;
+        std::vector<std::exception_ptr> err(nt);
+        for (int tr = 0; tr < nt; tr++)
+            th.emplace_back([&, tr] {
+                try {
+                    run(tr);
+                } catch (...) {
+                    err[tr] = std::current_exception();
+                }
+            });
+        for (auto &x : th) x.join();
+        for (auto &e : err)
+            if (e) std::rethrow_exception(e);
     }
-    return best;
+    int best = 0;
+    for (int tr = 1; tr < nt; tr++)
+        if (f[tr] < f[best]) best = tr;
+    return std::move(trees[best]);
 }
 
 std::vector<int> dynamic_slicing(CTree &t, int cap, int sa_beta_steps, uint64_t seed) {
