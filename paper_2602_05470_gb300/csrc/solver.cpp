@@ -439,30 +439,34 @@ void Solver::setup_host(const Problem &p, bool want_count) {
     out_ = SolveOutput();
 }
 
-// Contract every leaf sub-network (each a full contraction of the network with its
-// fixed variables sliced out). With counting, fold the results into the running
-// counting-sum in slot 0 (paper: the result is the sum over the branches);
-// without, only the leaves' maxima are computed (value planes only). Returns the
-// leaves' values.
-std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting,
-                                             const CTree *tree) {
-    const CTree &tr = tree ? *tree : tree_;
-    if (leaves.empty()) return {};
-    const int64_t n = (int64_t)leaves.size();
-    ensure_buffers(n + 1);   // slots 0..n, temporary at dcap_ > n
-    const uint64_t plane = (uint64_t)dcap_ + 1;
-    cudaEvent_t e0, e1;
-    BBTN_CUDA(cudaEventCreate(&e0));
-    BBTN_CUDA(cudaEventCreate(&e1));
-    BBTN_CUDA(cudaEventRecord(e0, stream_));
-    const double tw = now_s();
-    RunStats rs;
-    rs.tuner = opts_.autotune ? tuner_ : nullptr;
-    rs.prof = opts_.profile ? &prof_ : nullptr;
-    if (rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
+// Leaf contractions are enqueued in windows: window_open starts the timing, each
+// enqueue plans a list of leaves (host threads) and launches them without waiting
+// (leaf i of the list writes its root result to slot s0 + i), and window_close reads
+// the values back once. So the host goes on expanding the search tree or planning
+// the next leaves while the device contracts the previous ones.
+void Solver::window_open() {
+    if (win_.open) return;
+    BBTN_CUDA(cudaEventCreate(&win_.e0));
+    BBTN_CUDA(cudaEventCreate(&win_.e1));
+    BBTN_CUDA(cudaEventRecord(win_.e0, stream_));
+    win_.tw = now_s();
+    win_.rs = RunStats();
+    win_.rs.tuner = opts_.autotune ? tuner_ : nullptr;
+    win_.rs.prof = opts_.profile ? &prof_ : nullptr;
+    if (win_.rs.prof && !prof_.dump && getenv("BBTN_PROFILE_DUMP")) {
         prof_.dump = fopen(getenv("BBTN_PROFILE_DUMP"), "w");
         if (prof_.dump) fprintf(prof_.dump, "ra,rb,rc,rs,ident,bytes,ops,ms,kind,n\n");
     }
+    win_.open = true;
+}
+
+void Solver::enqueue_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting, const CTree *tree,
+                            int64_t s0) {
+    if (leaves.empty()) return;
+    const CTree &tr = tree ? *tree : tree_;
+    const int64_t n = (int64_t)leaves.size();
+    if (s0 + n > dcap_) fail(BBTN_ESTATE, "leaf result slots exhausted");
+    const uint64_t plane = (uint64_t)dcap_ + 1;
     // plan every leaf (host threads), then run them in groups that share launches:
     // leaf i of a group gets its own arena at i * stride
     const double tp = now_s();
@@ -477,33 +481,42 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
     }
     const uint64_t budget = arena_->owned ? std::max<uint64_t>(arena_budget_, arena_->size) : arena_->size;
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>({(int64_t)kBatchMax, (int64_t)(budget / stride), n}));
-    arena_->reserve(stride * nb);
+    arena_->reserve(stride * nb);   // growing frees the old arena, which waits for the device
     for (int64_t i0 = 0; i0 < n; i0 += nb) {
         std::vector<const Plan *> group;
         for (int64_t i = i0; i < std::min(n, i0 + nb); i++) group.push_back(&plans[i]);
-        run_plans(group, net_, arena_->ptr, stride, d_val_ + 1 + i0, d_cnt_ + 1 + i0, plane, stream_, &rs, &prog_);
+        run_plans(group, net_, arena_->ptr, stride, d_val_ + s0 + i0, d_cnt_ + s0 + i0, plane, stream_, &win_.rs,
+                  &prog_);
     }
-    if (counting) {
-        // slot 0 <- counting-sum of slots 0..n
+}
+
+// Ends the window: with `aggregate`, slot 0 <- counting-sum of slots 0..n (paper:
+// the result is the sum over the branches); returns the values of slots 1..n.
+std::vector<int32_t> Solver::window_close(int64_t n, bool aggregate) {
+    const uint64_t plane = (uint64_t)dcap_ + 1;
+    if (aggregate && n > 0) {
         int32_t *tv = d_val_ + dcap_;            // temporary result slot (last entry)
         uint64_t *tc = d_cnt_ + dcap_;
         cudaError_t e = launch_aggregate(n + 1, d_val_, d_cnt_, plane, np_, cprime_, tv, tc, plane, d_scratch_,
                                          stream_);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("aggregate: ") + cudaGetErrorString(e));
-        rs.launches += n + 1 > 256 ? 2 : 1;
+        win_.rs.launches += n + 1 > 256 ? 2 : 1;
         BBTN_CUDA(cudaMemcpyAsync(d_val_, tv, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
         for (int t = 0; t < np_; t++)
             BBTN_CUDA(cudaMemcpyAsync(d_cnt_ + t * plane, tc + t * plane, sizeof(uint64_t),
                                       cudaMemcpyDeviceToDevice, stream_));
     }
     std::vector<int32_t> vals(n);
-    BBTN_CUDA(cudaMemcpyAsync(vals.data(), d_val_ + 1, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream_));
-    BBTN_CUDA(cudaEventRecord(e1, stream_));
+    if (n > 0)
+        BBTN_CUDA(cudaMemcpyAsync(vals.data(), d_val_ + 1, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, stream_));
+    BBTN_CUDA(cudaEventRecord(win_.e1, stream_));
     BBTN_CUDA(cudaStreamSynchronize(stream_));
     float ms = 0;
-    BBTN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    BBTN_CUDA(cudaEventElapsedTime(&ms, win_.e0, win_.e1));
+    cudaEventDestroy(win_.e0);
+    cudaEventDestroy(win_.e1);
+    win_.open = false;
+    RunStats &rs = win_.rs;
     if (rs.prof) {
         prof_.collect();
         st_->prof_ms = prof_.ms;
@@ -525,18 +538,38 @@ std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_
         st_->prof_tcount_launches = prof_.tcount_launches;
     }
     st_->kernel_ms += ms;
-    st_->t_device_s += now_s() - tw;
+    st_->t_device_s += now_s() - win_.tw;
     st_->launches += rs.launches;
     st_->tropical_ops += rs.ops;
     st_->bytes_moved += rs.bytes;
-    if (counting) st_->leaves += n;
-    for (int64_t i = 0; i < n; i++) {
+    return vals;
+}
+
+// The best leaf and the incumbent after a window's values came back.
+void Solver::note_leaf_values(const std::vector<std::vector<int8_t>> &leaves, const std::vector<int32_t> &vals) {
+    for (size_t i = 0; i < vals.size(); i++) {
         if (vals[i] >= kFiniteMin && vals[i] > best_val_) {
             best_val_ = vals[i];
             best_fx_ = leaves[i];
         }
         incumbent_ = std::max<int64_t>(incumbent_, vals[i] >= kFiniteMin ? vals[i] : INT64_MIN);
     }
+}
+
+// Contract a list of leaf sub-networks and wait (each a full contraction of the
+// network with its fixed variables sliced out). With counting, fold the results
+// into the running counting-sum in slot 0; without, only the leaves' maxima are
+// computed (value planes only). Returns the leaves' values.
+std::vector<int32_t> Solver::contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting,
+                                             const CTree *tree) {
+    if (leaves.empty()) return {};
+    const int64_t n = (int64_t)leaves.size();
+    ensure_buffers(n + 1);   // slots 0..n, temporary at dcap_ > n
+    window_open();
+    enqueue_leaves(leaves, counting, tree, 1);
+    std::vector<int32_t> vals = window_close(n, counting);
+    if (counting) st_->leaves += n;
+    note_leaf_values(leaves, vals);
     return vals;
 }
 
@@ -696,22 +729,38 @@ void Solver::search(bool dry, BranchLog *log) {
     // are contracted again with counts -- the others add nothing to the count.
     std::vector<std::vector<int8_t>> cand;     // leaves that may attain the optimum
     std::vector<int32_t> cand_val;
+    // Value-only leaves go to the device in groups of up to kBatchMax as soon as a
+    // group is complete, without waiting; their maxima come back once `bs` leaves are
+    // in flight or the tree is exhausted (then the incumbent rises and prunes).
+    std::vector<std::vector<int8_t>> inflight;
+    if (!dry) ensure_buffers(std::max(bs, (int)kBatchMax) + 1);
+    auto flush = [&]() {
+        if (inflight.empty()) return;
+        std::vector<int32_t> v = window_close((int64_t)inflight.size(), np_ == 0);
+        if (np_ == 0) st_->leaves += (int64_t)inflight.size();
+        note_leaf_values(inflight, v);
+        if (np_ > 0) {
+            for (size_t i = 0; i < inflight.size(); i++)
+                if (v[i] >= kFiniteMin && v[i] >= incumbent_) {
+                    cand.push_back(std::move(inflight[i]));
+                    cand_val.push_back(v[i]);
+                }
+        }
+        inflight.clear();
+    };
     while (!stack.empty() || !batch.empty()) {
-        if (stack.empty() || (int)batch.size() >= bs) {
+        if (stack.empty() || (int)batch.size() >= kBatchMax) {
             if (dry) {
                 st_->leaves += (int64_t)batch.size();
                 batch.clear();
                 continue;
             }
-            std::vector<int32_t> v = contract_leaves(batch, np_ == 0);
-            if (np_ > 0) {
-                for (size_t i = 0; i < batch.size(); i++)
-                    if (v[i] >= kFiniteMin && v[i] >= incumbent_) {
-                        cand.push_back(std::move(batch[i]));
-                        cand_val.push_back(v[i]);
-                    }
-            }
+            if ((int64_t)(inflight.size() + batch.size()) + 1 > dcap_) flush();
+            window_open();
+            enqueue_leaves(batch, np_ == 0, nullptr, 1 + (int64_t)inflight.size());
+            for (auto &fx : batch) inflight.push_back(std::move(fx));
             batch.clear();
+            if ((int)inflight.size() >= bs || stack.empty()) flush();
             continue;
         }
         BNode nd = std::move(stack.back());
@@ -813,24 +862,43 @@ void Solver::search(bool dry, BranchLog *log) {
         }
         for (auto &ch : kids) stack.push_back(std::move(ch));   // best bound popped first
     }
+    flush();   // leaves still in flight when the last nodes were pruned
     if (np_ > 0) {
         std::vector<std::vector<int8_t>> opt;
         for (size_t i = 0; i < cand.size(); i++)
             if (cand_val[i] == incumbent_) opt.push_back(std::move(cand[i]));
         st_->pruned += (int64_t)(cand.size() - opt.size());
-        // counting leaves with an order of their own run alone; the others in batches
-        std::vector<std::vector<int8_t>> rest;
-        for (auto &fx : opt) {
-            CTree t;
-            const double tp = now_s();
-            const bool own = leaf_order(fx, t);
-            st_->t_plan_s += now_s() - tp;
-            if (own) contract_leaves({fx}, true, &t);
-            else rest.push_back(std::move(fx));
-        }
-        for (size_t i = 0; i < rest.size(); i += (size_t)bs) {
-            std::vector<std::vector<int8_t>> b(rest.begin() + i, rest.begin() + std::min(rest.size(), i + (size_t)bs));
-            contract_leaves(b, true);
+        // counting leaves with an order of their own run alone, the others in groups
+        // on the root order; each leaf's order is found while the device contracts
+        // the previous ones, and the counting-sum waits for all of them once
+        for (size_t i0 = 0; i0 < opt.size(); i0 += (size_t)bs) {
+            const size_t n = std::min(opt.size() - i0, (size_t)bs);
+            ensure_buffers((int64_t)n + 1);
+            window_open();
+            std::vector<std::vector<int8_t>> rest;
+            std::vector<int64_t> rest_slot;
+            int64_t slot = 1;
+            auto run_rest = [&]() {
+                for (size_t j = 0; j < rest.size(); j += kBatchMax) {
+                    const size_t m = std::min(rest.size() - j, (size_t)kBatchMax);
+                    std::vector<std::vector<int8_t>> g(rest.begin() + j, rest.begin() + j + m);
+                    enqueue_leaves(g, true, nullptr, slot);
+                    slot += (int64_t)m;
+                }
+                rest.clear();
+            };
+            for (size_t i = i0; i < i0 + n; i++) {
+                CTree t;
+                const double tp = now_s();
+                const bool own = leaf_order(opt[i], t);
+                st_->t_plan_s += now_s() - tp;
+                if (own) enqueue_leaves({opt[i]}, true, &t, slot++);
+                else rest.push_back(opt[i]);
+                if (rest.size() == (size_t)kBatchMax) run_rest();
+            }
+            run_rest();
+            window_close((int64_t)n, true);
+            st_->leaves += (int64_t)n;
         }
     }
 }

@@ -58,6 +58,17 @@ class Solver {
     void setup_host(const Problem &p, bool want_count);
     std::vector<int32_t> contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting = true,
                                          const CTree *tree = nullptr);
+    void window_open();
+    void enqueue_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting, const CTree *tree, int64_t s0);
+    std::vector<int32_t> window_close(int64_t n, bool aggregate);
+    void note_leaf_values(const std::vector<std::vector<int8_t>> &leaves, const std::vector<int32_t> &vals);
+    struct Window {
+        bool open = false;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        double tw = 0;
+        RunStats rs;
+    };
+    Window win_;
     bool leaf_order(const std::vector<int8_t> &fx, CTree &out);
     void finish(bool want_config);
     void run_plain();
