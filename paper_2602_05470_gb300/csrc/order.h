@@ -42,6 +42,10 @@ Cost tree_cost(const CTree &t, int cap, const std::vector<char> *removed = nullp
 CTree greedy_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, uint64_t seed,
                    double noise);
 
+// Contraction tree from a min-fill variable elimination order (bucket elimination:
+// the tensors holding the next variable are contracted together, smallest first).
+CTree elimination_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, uint64_t seed);
+
 struct SAParams {
     double beta_start = 1.0, beta_end = 15.0;
     int beta_steps = 20;
