@@ -414,6 +414,16 @@ int bbtn_set_gnn(bbtn_ctx *ctx, bbtn_gnn *branch_scorer, bbtn_gnn *value_model);
 int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, float *score, float *gamma,
                         int *rows);
 
+/*
+ * The leaf sub-networks of the branch-and-bound search of the loaded instance,
+ * expanded on the host as bbtn_analyze does (BBTN section: the leaves are the
+ * branches whose contractions are summed; only the heuristic incumbent prunes).
+ * Writes the fixings of the first min(max_leaves, leaves) leaves to fx (host
+ * int8[max_leaves * n], row per leaf: -1 free, 0 or 1 fixed) and the number of
+ * leaves of the whole search to *leaves. Host only.
+ */
+int bbtn_search_leaves(bbtn_ctx *ctx, int64_t max_leaves, int8_t *fx, int64_t *leaves);
+
 #ifdef __cplusplus
 }
 #endif

@@ -207,6 +207,16 @@ class Solver:
         r = rows.value
         return fx[:r], sc[:r], ga[:r]
 
+    def search_leaves(self, inst, max_leaves: int = 4096):
+        """Host-side search: (fixings of the first max_leaves leaves as an int8 array
+        leaves' x n, -1 free / 0 / 1; number of leaves of the whole search)."""
+        import numpy as np
+        self.load(inst)
+        fx = np.zeros((max_leaves, inst.n), dtype=np.int8)
+        total = C.c_int64()
+        check(_lib.load().bbtn_search_leaves(self._ctx, max_leaves, fx.ctypes.data_as(_lib._i8p), C.byref(total)))
+        return fx[:min(max_leaves, total.value)], total.value
+
     def load(self, inst):
         """inst: object with kind ('spin'|'mwis'), n, edges, J, h2, w (e.g. synth.Instance)."""
         lib = _lib.load()

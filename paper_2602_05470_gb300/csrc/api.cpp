@@ -653,4 +653,20 @@ int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, 
     });
 }
 
+int bbtn_search_leaves(bbtn_ctx *ctx, int64_t max_leaves, int8_t *fx, int64_t *leaves) {
+    return guarded([&] {
+        if (!ctx || !leaves || max_leaves < 0 || (max_leaves > 0 && !fx)) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        bbtn_opts o = ctx->opts;
+        o.mode = BBTN_MODE_BBTN;
+        Solver s(o, nullptr, &ctx->arena);
+        s.set_gnn(ctx->gnn_branch, nullptr);
+        bbtn_stats st{};
+        std::vector<int8_t> all;
+        s.search_leaves(ctx->prob, max_leaves, all, &st);
+        if (!all.empty()) memcpy(fx, all.data(), all.size());
+        *leaves = st.leaves;
+    });
+}
+
 }  // extern "C"

@@ -120,7 +120,8 @@ double branch_at(const Problem &p, const CTree &tree, int cap, const std::vector
                     if (fx[u] >= 0) eff += 2ll * p.J[nb.second] * (2 * fx[u] - 1);
                     else if (inR[u] && u > v) {
                         int j = (int)(std::find(R.begin(), R.end(), u) - R.begin());
-                        val += 2ll * p.J[nb.second] * (2 * xi - 1) * (2 * ((c >> j) & 1) - 1);
+                        const int xj = (int)((c >> j) & 1u);   // signed: 2 * xj - 1 is -1 or +1
+                        val += 2ll * p.J[nb.second] * (2 * xi - 1) * (2 * xj - 1);
                     }
                 }
                 val += eff * (2 * xi - 1);
@@ -751,6 +752,11 @@ void Solver::search(bool dry, BranchLog *log) {
     while (!stack.empty() || !batch.empty()) {
         if (stack.empty() || (int)batch.size() >= kBatchMax) {
             if (dry) {
+                if (leaf_log_)
+                    for (auto &fx : batch) {
+                        if ((int64_t)leaf_log_->size() >= leaf_log_max_ * (int64_t)p.n) break;
+                        leaf_log_->insert(leaf_log_->end(), fx.begin(), fx.end());
+                    }
                 st_->leaves += (int64_t)batch.size();
                 batch.clear();
                 continue;
@@ -1014,6 +1020,17 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
         }
         fclose(f);
     }
+}
+
+void Solver::search_leaves(const Problem &p, int64_t max_leaves, std::vector<int8_t> &fx, bbtn_stats *st) {
+    leaf_log_ = &fx;
+    leaf_log_max_ = max_leaves;
+    fx.clear();
+    bbtn_stats local{};
+    st_ = st ? st : &local;
+    setup_host(p, false);
+    search(true, nullptr);
+    leaf_log_ = nullptr;
 }
 
 void Solver::branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st) {

@@ -51,6 +51,8 @@ class Solver {
     }
     // dry search of the loaded problem with per-node lookahead records (host only)
     void branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st);
+    // dry search: the fixings of its leaf sub-networks, n per leaf (host only)
+    void search_leaves(const Problem &p, int64_t max_leaves, std::vector<int8_t> &fx, bbtn_stats *st);
 
   private:
     struct Leafset;
@@ -69,6 +71,8 @@ class Solver {
         RunStats rs;
     };
     Window win_;
+    std::vector<int8_t> *leaf_log_ = nullptr;   // search_leaves: leaf fixings
+    int64_t leaf_log_max_ = 0;
     bool leaf_order(const std::vector<int8_t> &fx, CTree &out);
     void finish(bool want_config);
     void run_plain();

@@ -161,3 +161,18 @@ def test_ksg_30x30_options_do_not_change_the_answer(P):
     tuned = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, autotune=True)
     for _ in range(2):
         _check(inst, tuned.solve(inst, count=True, config=False), row["alpha"], int(row["count"]))
+
+
+@pytest.mark.parametrize("row,cap", [(0, 10), (0, 14), (1, 10), (1, 12), (2, 14), (2, 16)])
+@pytest.mark.parametrize("use_symmetry", [True, False])
+def test_spin_large_bbtn_caps(P, row, cap, use_symmetry):
+    """16 x 16 and 20 x 20 +-J lattices (no field) under branch-and-bound at several
+    caps, with and without the spin-flip symmetry: energy, exact degeneracy (CRT)
+    and a ground state against the stored oracle answers."""
+    with open(GOLDEN) as f:
+        g = json.load(f)["spin_large_f6"][row]
+    inst = synth.square_lattice(g["L"], seed=g["seed"])
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap, use_symmetry=use_symmetry)
+    res = s.solve(inst, count=True, config=True)
+    _check(inst, res, g["e2"], int(g["count"]))
+    assert res.stats["sc_log2"] <= cap

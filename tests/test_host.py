@@ -152,3 +152,39 @@ def test_gnn_features_match_oracle(P, seed):
     want = G.features(inst.n, inst.edges, inst.w, fixed, score)
     np.testing.assert_allclose(got, want, rtol=1e-7, atol=0)
     assert gnn.GNN.param_count() == G.param_count()
+
+
+def _leaf_sum(P, inst, cap, use_symmetry):
+    """(E2, D) of an instance from the host search's leaves, each solved by the
+    transfer-matrix oracle with its fixed spins pinned by strong fields."""
+    import oracle
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap, use_symmetry=use_symmetry)
+    fx, total = s.search_leaves(inst, max_leaves=4096)
+    assert len(fx) == total > 0
+    big = 8 * (sum(abs(j) for j in inst.J) + 1)
+    best, count = None, 0
+    for row in fx:
+        h2 = [h + (big if f == 1 else -big if f == 0 else 0) for h, f in zip(inst.h2, row)]
+        leaf = synth.Instance(**{**inst.__dict__, "h2": h2})
+        e2, d, _ = oracle.spin_square_tm(leaf)
+        e2 += big * int((row >= 0).sum())
+        if best is None or e2 < best:
+            best, count = e2, 0
+        if e2 == best:
+            count += d
+    return best, count * (2 if use_symmetry else 1)
+
+
+@pytest.mark.parametrize("row,cap", [(0, 14), (1, 12)])
+@pytest.mark.parametrize("use_symmetry", [True, False])
+def test_search_leaves_cover_every_ground_state(P, row, cap, use_symmetry):
+    """The branch-and-bound leaves partition the optimal configurations: summing
+    the leaves' exact optima and degeneracies (oracle) gives the lattice's.
+    16 x 16 +-J lattices with stored oracle answers; regions of 8 spins, whose
+    local values (fields from fixed neighbours, couplings inside the region)
+    decide which configurations each branching keeps."""
+    import json
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_answers.json")) as f:
+        g = json.load(f)["spin_large_f6"][row]
+    inst = synth.square_lattice(g["L"], seed=g["seed"])
+    assert _leaf_sum(P, inst, cap, use_symmetry) == (g["e2"], int(g["count"]))
