@@ -176,3 +176,22 @@ def test_spin_large_bbtn_caps(P, row, cap, use_symmetry):
     res = s.solve(inst, count=True, config=True)
     _check(inst, res, g["e2"], int(g["count"]))
     assert res.stats["sc_log2"] <= cap
+
+
+def test_spin_32x32_cap26_count_and_ground_state(P):
+    """The 32 x 32 +-J lattice (no field) under branch-and-bound with a space cap of
+    2^26, counts as residues mod five primes plus the check prime, and one ground
+    state from the tropical backward pass. No oracle reaches this size, so the
+    checks are invariants: the configuration attains the returned energy, the
+    degeneracy is even (spin-flip symmetry), every tensor fits the cap, and the
+    CRT of the first three residues already gives the whole count (so the five
+    residues agree on one integer below the three-prime range)."""
+    inst = synth.square_lattice(32, seed=synth.config_seed(3, 0))
+    res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=26, n_primes=5).solve(inst, count=True, config=True)
+    assert res.stats["sc_log2"] <= 26
+    assert _energy(inst, res.config) == res.energy2
+    assert -2 * inst.m <= res.energy2 < 0
+    assert res.count > 0 and res.count % 2 == 0
+    assert P.crt(res.residues[:3], res.primes[:3]) == res.count
+    for r, p in zip(res.residues, res.primes):
+        assert r == res.count % p
