@@ -315,6 +315,8 @@ VEC = [
     (list(range(14)), [13, 20, 21], list(range(13)) + [20, 21], 0, 0),  # two B-only output bits on top
     (list(range(14)), [13, 20, 21], [21] + list(range(13)) + [20], 1, 1),  # B-only bits at 0 and top, shifted
     ([5, 0, 3, 1, 2, 4, 6, 7, 8, 9, 10, 11], [4, 30], [30, 0, 1, 2, 3] + list(range(5, 12)), 0, 0),  # scattered A
+    (list(range(14)), [12, 13], list(range(12)) + [13], 0, 0),        # B inside A: 128-bit residue loads/stores
+    (list(range(14)), [12, 13], list(range(12)) + [13], 1, 0),        # the same with A not 16-byte aligned
 ]
 
 
