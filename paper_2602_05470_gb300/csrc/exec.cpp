@@ -205,7 +205,7 @@ void Arena::release() {
 static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, FreeList &fl) {
     const int nsteps = (int)plan.steps.size();
     std::vector<char> fus(t.nodes.size(), 0);
-    const int S = np == 0 ? 12 : 10;
+    const int S = np == 0 ? 14 : 11;
     const uint64_t budget = 200 * 1024;
     if (!keep_all && np <= 4) {
         for (int i = 0; i < nsteps; i++) {
@@ -547,7 +547,7 @@ struct LaunchTimer {
     }
     void done(double bytes, double ops, const ContractParams *P, int kind, int n) {
         if (!pr) return;
-        if (kind == 2 && P) kind = P->np > 0 ? 5 : (P->v16 ? 4 : 2);
+        if (kind == 2 && P) kind = P->np > 0 ? 5 : (tiled_uses_v16(*P) ? 4 : 2);
         if ((kind == 0 || kind == 3) && P && P->np > 0) kind = 6;
         BBTN_CUDA(cudaEventRecord(b, s));
         int ra = 0, rb = 0, ident = 0, rc = 0, rs = 0;

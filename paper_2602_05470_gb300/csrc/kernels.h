@@ -63,6 +63,7 @@ cudaError_t launch_contract_stream4_batch(const ContractParams *p, int n, cudaSt
 // m / n; 0..3 = forced (bit 0: A along k, bit 1: B along k), as an autotuner picks it
 cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s, int lanes = -1);
 bool tiled_eligible(const ContractParams &p);
+bool tiled_uses_v16(const ContractParams &p);   // the value pass runs with two 16-bit lanes
 
 // out bit q <- in bit perm[q]
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,

@@ -6,7 +6,8 @@
 //
 // b, m, n, k are groups of binary labels (batch / A-only / B-only / summed); every
 // group is gathered through bit-deposit tables, so no permutation pass runs in front
-// of the step. A block computes a 64 x 64 output tile of one batch entry, 256
+// of the step. A block computes a 64 x 64 output tile of one batch entry (64 x 16
+// when the B-only group has only 4 or 5 labels, 4 x 1 per thread), 256
 // threads with a 4 x 4 micro-tile each, streaming K through shared memory in
 // chunks of 16 (int32 add + max, no tensor cores: max-plus is not an MMA). Values
 // only: the next chunk is prefetched into registers while the current one is
@@ -49,19 +50,21 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, const int8_t *pos, int n
 // (r < 4) of every TM x TK chunk, with lanes along the operand's contiguous group.
 // Row / column offsets and the in-chunk k offsets do not change from chunk to
 // chunk, so they are summed once; a chunk only adds the deposit of its first k.
+template <int R>
 struct Lanes {
-    uint32_t off[4];    // element offset of (row, k in chunk)
-    uint32_t sidx[4];   // shared-memory index ki * (T + 4) + mi
+    uint32_t off[R];    // element offset of (row, k in chunk)
+    uint32_t sidx[R];   // shared-memory index ki * (ROWS + 4) + mi
 };
 
-__device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32_t *koff, int fast_k, Lanes &L) {
+template <int ROWS, int R>
+__device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32_t *koff, int fast_k, Lanes<R> &L) {
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
+    for (int r = 0; r < R; r++) {
         const int e = threadIdx.x + r * kThr;
-        const int mi = fast_k ? (e >> 4) : (e & (TM - 1));
-        const int ki = fast_k ? (e & (TK - 1)) : (e >> 6);
+        const int mi = fast_k ? (e >> 4) : (e & (ROWS - 1));
+        const int ki = fast_k ? (e & (TK - 1)) : (e / ROWS);
         L.off[r] = rowoff[mi] + koff[ki];       // ki < 16: first byte table only
-        L.sidx[r] = (uint32_t)(ki * (TM + 4) + mi);
+        L.sidx[r] = (uint32_t)(ki * (ROWS + 4) + mi);
     }
 }
 
@@ -70,20 +73,19 @@ __device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32
 __device__ __forceinline__ uint32_t chunk_off(const uint32_t *koff, int k0) { return kof(koff, (uint32_t)k0); }
 
 // load one chunk of values (and counts) into shared memory as [k][m]
-template <int NP>
+template <int NP, int ROWS, int R>
 __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
-                                          uint64_t plane, int unit, const Lanes &L, uint32_t kb,
-                                          int32_t *sv, uint64_t (*sc)[TK][TM + 2]) {
+                                          uint64_t plane, int unit, const Lanes<R> &L, uint32_t kb,
+                                          int32_t *sv, uint64_t *sc) {
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
+    for (int r = 0; r < R; r++) {
         const uint32_t off = L.off[r] + kb;
         const int32_t x = __ldg(v + off);
         sv[L.sidx[r]] = x;
         if constexpr (NP > 0) {
-            uint64_t *scf = &sc[0][0][0];
 #pragma unroll
             for (int t = 0; t < NP; t++)
-                scf[t * TK * (TM + 2) + (L.sidx[r] / (TM + 4)) * (TM + 2) + L.sidx[r] % (TM + 4)] =
+                sc[t * TK * (ROWS + 2) + (L.sidx[r] / (ROWS + 4)) * (ROWS + 2) + L.sidx[r] % (ROWS + 4)] =
                     unit ? (x >= kFiniteMin ? 1ull : 0ull) : __ldg(c + (uint64_t)t * plane + off);
         }
     }
@@ -96,11 +98,16 @@ constexpr int32_t kFinite16 = -(1 << 13);
 __device__ __forceinline__ int32_t to16(int32_t x) { return x >= kFiniteMin ? x : kNeg16; }
 __device__ __forceinline__ uint32_t dup16(int32_t x) { return ((uint32_t)x & 0xffffu) | ((uint32_t)x << 16); }
 
-template <int NP, bool V16>
+template <int NP, bool V16, int TN>
 __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups &G, int fastA_k, int fastB_k,
                                            uint64_t tile, unsigned char *smem_raw) {
     // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
-    // sB[TK][TN+4], counts
+    // sB[TK][TN+4], counts. TN = 64: 4 x 4 outputs per thread; TN = 16: 4 x 1.
+    static_assert(TN == 64 || TN == 16, "column tile");
+    static_assert(!V16 || TN == 64, "16-bit lanes pair columns");
+    constexpr int MC = TN / 16;              // columns per thread
+    constexpr int RB = TN * TK / kThr;       // B elements a thread loads per chunk
+    constexpr int TNB = TN == 64 ? 6 : 4;    // column bits of a tile
     const int K = 1 << G.nk;
     uint32_t *koffA = (uint32_t *)smem_raw;
     uint32_t *koffB = koffA + 768;
@@ -114,7 +121,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     uint64_t(*cB)[TK][TN + 2] = (uint64_t(*)[TK][TN + 2])((uint64_t *)cA + (NP > 0 ? NP : 1) * TK * (TM + 2));
 
     const int mt = 1 << (G.nm > 6 ? G.nm - 6 : 0);
-    const int nt = 1 << (G.nn > 6 ? G.nn - 6 : 0);
+    const int nt = 1 << (G.nn - TNB);
     const int tn = (int)(tile % nt);
     const int tm = (int)((tile / nt) % mt);
     const uint64_t b = tile / ((uint64_t)nt * mt);
@@ -138,20 +145,21 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     }
     __syncthreads();
 
-    Lanes LA, LB;
-    lanes_setup(rowA, koffA, fastA_k, LA);
-    lanes_setup(colB, koffB, fastB_k, LB);
+    Lanes<4> LA;
+    Lanes<RB> LB;
+    lanes_setup<TM, 4>(rowA, koffA, fastA_k, LA);
+    lanes_setup<TN, RB>(colB, koffB, fastB_k, LB);
     const int32_t *__restrict__ Av = P.A.val + baseA;
     const int32_t *__restrict__ Bv = P.B.val + baseB;
     const uint64_t *__restrict__ Ac = P.A.cnt ? P.A.cnt + baseA : nullptr;
     const uint64_t *__restrict__ Bc = P.B.cnt ? P.B.cnt + baseB : nullptr;
 
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 each
-    int32_t best[4][4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x MC each
+    int32_t best[4][MC];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) best[i][j] = kNeg;
+        for (int j = 0; j < MC; j++) best[i][j] = kNeg;
 
     if constexpr (V16) {
         // values only, two 16-bit lanes per instruction: A is stored duplicated into
@@ -161,24 +169,22 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         uint32_t best2[4][2];
 #pragma unroll
         for (int i = 0; i < 4; i++) best2[i][0] = best2[i][1] = dup16(kNeg16);
-        int32_t ra[4], rb[4];
+        int32_t ra[4], rb[RB];
         auto gload = [&](int k0) {
             const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                ra[r] = __ldg(Av + LA.off[r] + ka);
-                rb[r] = __ldg(Bv + LB.off[r] + kb);
-            }
+            for (int r = 0; r < 4; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
+#pragma unroll
+            for (int r = 0; r < RB; r++) rb[r] = __ldg(Bv + LB.off[r] + kb);
         };
         int32_t *sAf = &sA[0][0];
         uint16_t *sB16f = &sB16[0][0];
         auto sstore = [&]() {
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                sAf[LA.sidx[r]] = (int32_t)dup16(to16(ra[r]));
-                // same (k, n) position in the int16 tile, whose rows are TN + 8 wide
+            for (int r = 0; r < 4; r++) sAf[LA.sidx[r]] = (int32_t)dup16(to16(ra[r]));
+#pragma unroll
+            for (int r = 0; r < RB; r++)   // same (k, n) position in the int16 tile, rows TN + 8 wide
                 sB16f[(LB.sidx[r] / (TN + 4)) * (TN + 8) + LB.sidx[r] % (TN + 4)] = (uint16_t)to16(rb[r]);
-            }
         };
         gload(0);
         for (int k0 = 0; k0 < K; k0 += TK) {
@@ -209,22 +215,20 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         // values only: int32 add + max. The next chunk's tiles are fetched into
         // registers while the current chunk is computed from shared memory.
         {
-            int32_t ra[4], rb[4];
+            int32_t ra[4], rb[RB];
             auto gload = [&](int k0) {
                 const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    ra[r] = __ldg(Av + LA.off[r] + ka);
-                    rb[r] = __ldg(Bv + LB.off[r] + kb);
-                }
+                for (int r = 0; r < 4; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
+#pragma unroll
+                for (int r = 0; r < RB; r++) rb[r] = __ldg(Bv + LB.off[r] + kb);
             };
             int32_t *sAf = &sA[0][0], *sBf = &sB[0][0];
             auto sstore = [&]() {
 #pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    sAf[LA.sidx[r]] = ra[r];
-                    sBf[LB.sidx[r]] = rb[r];
-                }
+                for (int r = 0; r < 4; r++) sAf[LA.sidx[r]] = ra[r];
+#pragma unroll
+                for (int r = 0; r < RB; r++) sBf[LB.sidx[r]] = rb[r];
             };
             gload(0);
             for (int k0 = 0; k0 < K; k0 += TK) {
@@ -235,55 +239,65 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                 for (int kk = 0; kk < TK; kk++) {
                     const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
-                    const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
                     const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-                    const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+                    int bb[MC];
+                    if constexpr (MC == 4) {
+                        const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                        bb[0] = b4.x; bb[1] = b4.y; bb[2] = b4.z; bb[3] = b4.w;
+                    } else {
+                        bb[0] = sB[kk][tx];
+                    }
 #pragma unroll
                     for (int i = 0; i < 4; i++)
 #pragma unroll
-                        for (int j = 0; j < 4; j++) best[i][j] = __viaddmax_s32(a[i], bb[j], best[i][j]);
+                        for (int j = 0; j < MC; j++) best[i][j] = __viaddmax_s32(a[i], bb[j], best[i][j]);
                 }
             }
         }
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
-            for (int j = 0; j < 4; j++) P.vc[baseC + rowC[ty * 4 + i] + colC[tx * 4 + j]] = best[i][j];
+            for (int j = 0; j < MC; j++) P.vc[baseC + rowC[ty * 4 + i] + colC[tx * MC + j]] = best[i][j];
     } else {
         // values and counts in one pass over K. Per chunk: the chunk maximum of each
         // output; a larger one restarts the count, an equal one adds the products of
         // the chunk's maximising k (summed as 128-bit integers, reduced once).
-        uint64_t acc[4][4][NP];
+        uint64_t acc[4][MC][NP];
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
-            for (int j = 0; j < 4; j++)
+            for (int j = 0; j < MC; j++)
 #pragma unroll
                 for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
         for (int k0 = 0; k0 < K; k0 += TK) {
-            load_tile<NP>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], cA);
-            load_tile<NP>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], cB);
+            load_tile<NP, TM, 4>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], &cA[0][0][0]);
+            load_tile<NP, TN, RB>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], &cB[0][0][0]);
             __syncthreads();
-            int32_t cm[4][4];
+            int32_t cm[4][MC];
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) cm[i][j] = kNeg;
+                for (int j = 0; j < MC; j++) cm[i][j] = kNeg;
 #pragma unroll
             for (int kk = 0; kk < TK; kk++) {
                 const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
-                const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
                 const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-                const int bb[4] = {b4.x, b4.y, b4.z, b4.w};
+                int bb[MC];
+                if constexpr (MC == 4) {
+                    const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                    bb[0] = b4.x; bb[1] = b4.y; bb[2] = b4.z; bb[3] = b4.w;
+                } else {
+                    bb[0] = sB[kk][tx];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) cm[i][j] = __viaddmax_s32(a[i], bb[j], cm[i][j]);
+                    for (int j = 0; j < MC; j++) cm[i][j] = __viaddmax_s32(a[i], bb[j], cm[i][j]);
             }
 #pragma unroll
             for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
+                for (int j = 0; j < MC; j++) {
                     if (cm[i][j] > best[i][j]) {
                         best[i][j] = cm[i][j];
 #pragma unroll
@@ -293,7 +307,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                         u128 part[NP];
 #pragma unroll
                         for (int t = 0; t < NP; t++) part[t] = 0;
-                        const int mi = ty * 4 + i, nj = tx * 4 + j;
+                        const int mi = ty * 4 + i, nj = tx * MC + j;
                         for (int kk = 0; kk < TK; kk++) {
                             if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
 #pragma unroll
@@ -309,8 +323,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
         for (int i = 0; i < 4; i++)
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint64_t o = baseC + rowC[ty * 4 + i] + colC[tx * 4 + j];
+            for (int j = 0; j < MC; j++) {
+                const uint64_t o = baseC + rowC[ty * 4 + i] + colC[tx * MC + j];
                 P.vc[o] = best[i][j];
 #pragma unroll
                 for (int t = 0; t < NP; t++) P.cc[(uint64_t)t * P.planeC + o] = acc[i][j][t];
@@ -330,11 +344,11 @@ struct TArgs {
     Groups g[NB];
 };
 
-template <int NP, int NB, bool V16>
+template <int NP, int NB, bool V16, int TNC>
 __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
-        tiled_body<NP, V16>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
+        tiled_body<NP, V16, TNC>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
     } else {
         __shared__ ContractParams sP;
         __shared__ Groups sG;
@@ -345,18 +359,20 @@ __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_co
         const unsigned char *gsrc = (const unsigned char *)&args.g[e];
         for (int i = threadIdx.x; i < (int)sizeof(Groups); i += blockDim.x) ((unsigned char *)&sG)[i] = gsrc[i];
         __syncthreads();
-        tiled_body<NP, V16>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
+        tiled_body<NP, V16, TNC>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
     }
 }
 
-size_t tiled_smem(int nk, int np) {
-    (void)nk;
-    size_t s = 2 * 768 * 4 + 2 * (TM + TN) * 4 + TK * (TM + 4) * 4 + TK * (TN + 4) * 4 + 16;
-    if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (TN + 2) * 8;   // count tiles
+size_t tiled_smem(int np, int tn) {
+    size_t s = 2 * 768 * 4 + 2 * (TM + tn) * 4 + TK * (TM + 4) * 4 + TK * (tn + 4) * 4 + 16;
+    if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (tn + 2) * 8;   // count tiles
     return s;
 }
 
-template <int NP, int NB, bool V16>
+// column tile of a step: 64 when its B-only group has at least 6 labels, else 16
+inline int column_tile(const Groups &g) { return g.nn >= 6 ? 64 : 16; }
+
+template <int NP, int NB, bool V16, int TNC>
 cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, const int *fb, int n, cudaStream_t s) {
     TArgs<NB> a;
     memset(&a, 0, sizeof a);
@@ -365,7 +381,7 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
     for (int i = 0; i < n; i++) {
         const Groups &g = gs[i];
         a.blk0[i] = (uint32_t)total;
-        total += (1ull << g.nb) * (1ull << (g.nm - 6)) * (1ull << (g.nn - 6));
+        total += (1ull << g.nb) * (1ull << (g.nm - 6)) * (1ull << (g.nn - (TNC == 64 ? 6 : 4)));
         if (total > 0x7fffffffull) return cudaErrorInvalidValue;
         a.p[i] = ps[i];
         a.g[i] = g;
@@ -373,10 +389,11 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
         a.fb[i] = (int8_t)fb[i];
     }
     a.blk0[n] = (uint32_t)total;
-    const size_t smem = tiled_smem(0, NP);
-    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = tiled_smem(NP, TNC);
+    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16, TNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    k_tiled<NP, NB, V16><<<(unsigned)total, kThr, smem, s>>>(a);
+    k_tiled<NP, NB, V16, TNC><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -405,26 +422,59 @@ bool make_groups(const ContractParams &p, Groups &g, int &fa, int &fb) {
         g.kB[g.nk] = p.sB[j];
         g.nk++;
     }
-    if (g.nm < 6 || g.nn < 6 || g.nk < 4 || g.nk > 24) return false;
+    if (g.nm < 6 || g.nn < 4 || g.nk < 4 || g.nk > 24) return false;
     // lanes along k when the operand's bit 0 is a summed label, else along m / n
     fa = bitA0 == 0;
     fb = bitB0 == 0;
     return true;
 }
 
-template <int NB>
+template <int NB, int TNC>
 cudaError_t dispatch_t(const ContractParams *p, const Groups *g, const int *fa, const int *fb, int n, cudaStream_t s) {
+    const bool v16 = TNC == 64 && p[0].v16;
     switch (p[0].np) {
-        case 0: return p[0].v16 ? launch_t<0, NB, true>(p, g, fa, fb, n, s) : launch_t<0, NB, false>(p, g, fa, fb, n, s);
-        case 1: return launch_t<1, NB, false>(p, g, fa, fb, n, s);
-        case 2: return launch_t<2, NB, false>(p, g, fa, fb, n, s);
-        case 3: return launch_t<3, NB, false>(p, g, fa, fb, n, s);
-        case 4: return launch_t<4, NB, false>(p, g, fa, fb, n, s);
+        case 0: return v16 ? launch_t<0, NB, true, 64>(p, g, fa, fb, n, s) : launch_t<0, NB, false, TNC>(p, g, fa, fb, n, s);
+        case 1: return launch_t<1, NB, false, TNC>(p, g, fa, fb, n, s);
+        case 2: return launch_t<2, NB, false, TNC>(p, g, fa, fb, n, s);
+        case 3: return launch_t<3, NB, false, TNC>(p, g, fa, fb, n, s);
+        case 4: return launch_t<4, NB, false, TNC>(p, g, fa, fb, n, s);
         default: return cudaErrorNotSupported;
     }
 }
 
+// entries with 64- and 16-wide column tiles go out in separate launches
+template <int NB>
+cudaError_t dispatch_split(const ContractParams *p, const Groups *g, const int *fa, const int *fb, int n, cudaStream_t s) {
+    ContractParams pp[2][kBatchMax];
+    Groups gg[2][kBatchMax];
+    int ffa[2][kBatchMax], ffb[2][kBatchMax], cnt[2] = {0, 0};
+    for (int i = 0; i < n; i++) {
+        const int w = column_tile(g[i]) == 64 ? 0 : 1;
+        pp[w][cnt[w]] = p[i];
+        gg[w][cnt[w]] = g[i];
+        ffa[w][cnt[w]] = fa[i];
+        ffb[w][cnt[w]] = fb[i];
+        cnt[w]++;
+    }
+    for (int w = 0; w < 2; w++) {
+        if (!cnt[w]) continue;
+        cudaError_t e;
+        if (cnt[w] == 1) e = w ? dispatch_t<1, 16>(pp[w], gg[w], ffa[w], ffb[w], 1, s)
+                               : dispatch_t<1, 64>(pp[w], gg[w], ffa[w], ffb[w], 1, s);
+        else e = w ? dispatch_t<NB, 16>(pp[w], gg[w], ffa[w], ffb[w], cnt[w], s)
+                   : dispatch_t<NB, 64>(pp[w], gg[w], ffa[w], ffb[w], cnt[w], s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
+
+bool tiled_uses_v16(const ContractParams &p) {
+    Groups g;
+    int fa, fb;
+    return p.np == 0 && p.v16 && make_groups(p, g, fa, fb) && column_tile(g) == 64;
+}
 
 bool tiled_eligible(const ContractParams &p) {
     Groups g;
@@ -438,7 +488,7 @@ cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
     Groups g;
     int fa, fb;
     if (!make_groups(p, g, fa, fb)) return cudaErrorNotSupported;
-    return dispatch_t<1>(&p, &g, &fa, &fb, 1, s);
+    return dispatch_split<1>(&p, &g, &fa, &fb, 1, s);
 }
 
 cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s, int lanes) {
@@ -454,8 +504,8 @@ cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStre
             fb[i] = (lanes >> 1) & 1;
         }
     }
-    if (n == 1) return dispatch_t<1>(p, g, fa, fb, 1, s);
-    return dispatch_t<kBatchMax>(p, g, fa, fb, n, s);
+    if (n == 1) return dispatch_split<1>(p, g, fa, fb, 1, s);
+    return dispatch_split<kBatchMax>(p, g, fa, fb, n, s);
 }
 
 }  // namespace bbtn

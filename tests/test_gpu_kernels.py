@@ -98,6 +98,8 @@ TILED = [
     (7, 6, 6, 2, "k", "k", "bnm"),
     (6, 7, 5, 0, "m", "n", "mn"),
     (6, 6, 8, 0, "k", "k", "nm"),
+    (6, 4, 6, 2, "m", "k", "mnb"),       # 4 B-only labels: 64 x 16 tiles
+    (7, 5, 8, 1, "k", "n", "bnm"),       # 5 B-only labels
 ]
 
 
