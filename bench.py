@@ -275,10 +275,10 @@ def run_ours(args, rank, world, local_rank):
               pb["prof_scount_ms"], pb["prof_scount_bytes"], pb["prof_scount_launches"], peak, "GB/s",
               peak_kind + " HBM copy", 1e6),
         entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
-              "k_tiled<0, 16, 1>" if all16 else "k_tiled<0, 16, 0>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
+              "k_tiled<0, 16, 1, 64>" if all16 else "k_tiled<0, 16, 0, 64>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
               pb["prof_tiled_launches"], ALU_PEAK_TOPS * (2 if all16 else 1), "T tropical ops/s",
               alu_src + (" x 2 lanes" if all16 else ""), 1e9),
-        entry("k_tiled counting (register-tiled, K1t, 4 residue planes)", "k_tiled<4, 1, 0>", "alu",
+        entry("k_tiled counting (register-tiled, K1t, 4 residue planes)", "k_tiled<4, 1, 0, 64>", "alu",
               pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], ALU_PEAK_TOPS,
               "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
     ]
@@ -345,6 +345,10 @@ KERNEL_CASES = {
               list(range(0, 11)) + list(range(40, 51)) + [60, 61], 0),
     "tiled_count": (list(range(0, 10)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 50)) + [60, 61],
                     list(range(0, 10)) + list(range(40, 50)) + [60, 61], 4),
+    # a big x big step with only 4 B-only labels (64 x 16 tiles): batch 4, m 8, n 4, k 12
+    "tiled_narrow": (list(range(0, 8)) + list(range(20, 32)) + [60, 61, 62, 63],
+                     list(range(20, 32)) + list(range(40, 44)) + [60, 61, 62, 63],
+                     list(range(0, 8)) + list(range(40, 44)) + [60, 61, 62, 63], 0),
     # the same big x big step with 16-bit lanes (value-only leaves of small-range instances)
     "tiled16": (list(range(0, 11)) + list(range(20, 30)) + [60, 61], list(range(20, 30)) + list(range(40, 51)) + [60, 61],
                 list(range(0, 11)) + list(range(40, 51)) + [60, 61], -1),
