@@ -415,6 +415,21 @@ int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, 
                         int *rows);
 
 /*
+ * Host-only preparation of the loaded instance: builds its network and finds the
+ * root contraction order with ctx's options, leaving the order in a process-wide
+ * cache (keyed by the network's tensor labels, the root's fixed variables and the
+ * order-finder settings; at most 256 entries). A later bbtn_solve of an instance
+ * with the same structure and options, in any context, reuses it. Thread-safe with
+ * respect to solves on other contexts, so the order of the next instance can be
+ * found while the current one runs on the device. Uses no GPU.
+ */
+int bbtn_prepare(bbtn_ctx *ctx);
+
+/* Empties the process-wide cache of root contraction orders (e.g. to time solves
+ * that find their orders themselves). */
+int bbtn_clear_order_cache(void);
+
+/*
  * The leaf sub-networks of the branch-and-bound search of the loaded instance,
  * expanded on the host as bbtn_analyze does (BBTN section: the leaves are the
  * branches whose contractions are summed; only the heuristic incumbent prunes).

@@ -23,8 +23,13 @@ from . import _lib
 from ._lib import (BBTNError, FINITE_MIN, MAX_PRIMES, MODE_BBTN, MODE_PLAIN, MODE_SLICED, NEG,  # noqa: F401
                    Opts, Stats, check, i32_array, u64_array)
 
-__all__ = ["primes", "crt", "contract", "contract_values16", "permute", "aggregate", "contract_backward", "Solver", "Result",
+__all__ = ["clear_order_cache", "primes", "crt", "contract", "contract_values16", "permute", "aggregate", "contract_backward", "Solver", "Result",
            "BBTNError", "NEG", "FINITE_MIN", "MODE_PLAIN", "MODE_SLICED", "MODE_BBTN", "lib_path"]
+
+
+def clear_order_cache():
+    """Empty the library's process-wide cache of root contraction orders."""
+    check(_lib.load().bbtn_clear_order_cache())
 
 
 def lib_path() -> str:
@@ -206,6 +211,13 @@ class Solver:
                                               sc.ctypes.data_as(f32), ga.ctypes.data_as(f32), C.byref(rows)))
         r = rows.value
         return fx[:r], sc[:r], ga[:r]
+
+    def prepare(self, inst):
+        """Host-only: find the instance's root contraction order into the library's
+        order cache (a later solve of the same structure reuses it). Releases the GIL
+        while it runs, so it can overlap another context's solve."""
+        self.load(inst)
+        check(_lib.load().bbtn_prepare(self._ctx))
 
     def search_leaves(self, inst, max_leaves: int = 4096):
         """Host-side search: (fixings of the first max_leaves leaves as an int8 array

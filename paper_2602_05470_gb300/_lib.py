@@ -78,6 +78,8 @@ _SIGS = {
     "bbtn_contract_values16": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, _vp], C.c_int),
     "bbtn_permute": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
     "bbtn_search_leaves": ([_vp, C.c_int64, _i8p, _P(C.c_int64)], C.c_int),
+    "bbtn_prepare": ([_vp], C.c_int),
+    "bbtn_clear_order_cache": ([], C.c_int),
     "bbtn_aggregate": ([C.c_int64, _vp, _vp, C.c_int, _u64p, _vp, _vp, _vp], C.c_int),
     "bbtn_contract_backward": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp,
                                 C.c_int64, _vp, _vp, _vp, _vp], C.c_int),

@@ -653,6 +653,20 @@ int bbtn_branch_samples(bbtn_ctx *ctx, int max_rows, int lookahead, int8_t *fx, 
     });
 }
 
+int bbtn_clear_order_cache(void) {
+    return guarded([&] { clear_order_cache(); });
+}
+
+int bbtn_prepare(bbtn_ctx *ctx) {
+    return guarded([&] {
+        if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        Solver s(ctx->opts, nullptr, &ctx->arena);
+        bbtn_stats st{};
+        s.prepare(ctx->prob, &st);
+    });
+}
+
 int bbtn_search_leaves(bbtn_ctx *ctx, int64_t max_leaves, int8_t *fx, int64_t *leaves) {
     return guarded([&] {
         if (!ctx || !leaves || max_leaves < 0 || (max_leaves > 0 && !fx)) fail(BBTN_EINVAL, "bad arguments");

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <cstdlib>
 #include <exception>
+#include <mutex>
+#include <unordered_map>
 #include <functional>
 #include <thread>
 
@@ -338,6 +340,68 @@ void Solver::release_buffers() {
     dcap_ = 0;
 }
 
+namespace {
+
+// Contraction orders already found, by network structure and search settings: a
+// second solve (or an earlier host-only analysis, e.g. of the next instance on
+// another thread) reuses the tree instead of searching again. Bounded; cleared
+// when full.
+struct OrderCache {
+    std::mutex mu;
+    std::unordered_map<uint64_t, CTree> trees;
+};
+OrderCache &order_cache() {
+    static OrderCache c;
+    return c;
+}
+
+uint64_t order_key(const std::vector<std::vector<int>> &labels, const std::vector<int8_t> &fx, int cap,
+                   double w_rho, int trials, int sa_iters, uint64_t seed) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t x) {
+        h ^= x + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+        h *= 1099511628211ull;
+    };
+    mix(labels.size());
+    for (const auto &l : labels) {
+        mix(l.size());
+        for (int v : l) mix((uint64_t)v);
+    }
+    mix(fx.size());
+    for (int8_t f : fx) mix((uint64_t)(uint8_t)f);
+    mix((uint64_t)cap);
+    mix((uint64_t)(w_rho * 1024));
+    mix((uint64_t)trials);
+    mix((uint64_t)sa_iters);
+    mix(seed);
+    return h;
+}
+
+}  // namespace
+
+void clear_order_cache() {
+    OrderCache &c = order_cache();
+    std::lock_guard<std::mutex> lock(c.mu);
+    c.trees.clear();
+}
+
+// The root order: from the cache when this network (labels of its tensors and
+// the root's fixed variables) was ordered before with the same settings.
+CTree Solver::cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials) {
+    const uint64_t key = order_key(net_.labels, fx, cap, w_rho, trials, opts_.sa_iters, opts_.seed);
+    OrderCache &c = order_cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        auto it = c.trees.find(key);
+        if (it != c.trees.end()) return it->second;
+    }
+    CTree t = order_for(fx, cap, w_rho, trials);
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (c.trees.size() >= 256) c.trees.clear();
+    c.trees[key] = t;
+    return t;
+}
+
 CTree Solver::order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials) {
     std::vector<std::vector<int>> ll(net_.labels.size());
     for (size_t i = 0; i < ll.size(); i++)
@@ -429,7 +493,7 @@ void Solver::setup_host(const Problem &p, bool want_count) {
     const double t0 = now_s();
     const int cap = opts_.space_cap_log2;
     const double w_rho = opts_.mode == BBTN_MODE_PLAIN ? 8.0 : 1.0;
-    tree_ = order_for(fx0_, cap, w_rho, opts_.mode == BBTN_MODE_PLAIN ? 4 : 4);
+    tree_ = cached_order(fx0_, cap, w_rho, 4);
     Cost c = tree_cost(tree_, cap);
     st_->tc_log2 = c.tc_log2;
     st_->sc_plain_log2 = c.sc;
@@ -1020,6 +1084,12 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
         }
         fclose(f);
     }
+}
+
+void Solver::prepare(const Problem &p, bbtn_stats *st) {
+    bbtn_stats local{};
+    st_ = st ? st : &local;
+    setup_host(p, true);
 }
 
 void Solver::search_leaves(const Problem &p, int64_t max_leaves, std::vector<int8_t> &fx, bbtn_stats *st) {

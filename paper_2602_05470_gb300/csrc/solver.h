@@ -15,6 +15,9 @@
 
 namespace bbtn {
 
+// Empties the process-wide cache of root contraction orders.
+void clear_order_cache();
+
 struct SolveOutput {
     int64_t value = 0;                 // max-plus value of the network (-2H* or alpha)
     std::vector<uint64_t> res;         // residues (CRT primes first, check prime last if used)
@@ -51,6 +54,8 @@ class Solver {
     }
     // dry search of the loaded problem with per-node lookahead records (host only)
     void branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st);
+    // host-only set-up: instance network and root contraction order (into the order cache)
+    void prepare(const Problem &p, bbtn_stats *st);
     // dry search: the fixings of its leaf sub-networks, n per leaf (host only)
     void search_leaves(const Problem &p, int64_t max_leaves, std::vector<int8_t> &fx, bbtn_stats *st);
 
@@ -83,6 +88,7 @@ class Solver {
     int64_t incumbent_learned();
     void simplify(std::vector<int8_t> &fx) const;
     CTree order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
+    CTree cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
 
     bbtn_opts opts_;
     cudaStream_t stream_;
