@@ -188,3 +188,24 @@ def test_search_leaves_cover_every_ground_state(P, row, cap, use_symmetry):
         g = json.load(f)["spin_large_f6"][row]
     inst = synth.square_lattice(g["L"], seed=g["seed"])
     assert _leaf_sum(P, inst, cap, use_symmetry) == (g["e2"], int(g["count"]))
+
+
+def test_prepared_order_is_reused_and_identical(P):
+    """bbtn_prepare leaves the root order in the process-wide cache: a later plan of
+    the same network reuses it (same tree cost, much faster) and clearing the cache
+    makes the planner search again for the same tree."""
+    import time
+    inst = synth.kings_subgraph(20, 0.8, seed=11)
+    P.clear_order_cache()
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=16)
+    t0 = time.perf_counter()
+    s.prepare(inst)
+    t_first = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    s.prepare(inst)
+    t_cached = time.perf_counter() - t0
+    a = s.analyze(inst)
+    P.clear_order_cache()
+    b = P.Solver(mode=P.MODE_BBTN, space_cap_log2=16).analyze(inst)
+    assert a == b
+    assert t_cached < t_first
