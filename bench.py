@@ -189,7 +189,7 @@ def run_ours(args, rank, world, local_rank):
 
     def make_solver(profile=False):
         return P.Solver(mode=P.MODE_BBTN, space_cap_log2=CAP, n_primes=3, batch=64, profile=profile,
-                        stream=stream.cuda_stream)
+                        leaf_trials=args.leaf_trials, stream=stream.cuda_stream)
 
     solver = make_solver()
     # host-side helper: finds the next instance's contraction order (into the
@@ -221,7 +221,8 @@ def run_ours(args, rank, world, local_rank):
                 th.join()
             if timed:
                 per_inst_ms[idx] = ea.elapsed_time(eb)
-            for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms"):
+            for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms", "t_plan_s",
+                      "t_device_s", "t_total_s"):
                 st_sum[k] = st_sum.get(k, 0) + res.stats[k]
             h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
             d2h += 4 * (res.stats["leaves"] + res.stats["nodes"]) + 4 + 8 * 4   # leaf maxima + result
@@ -257,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
     ck = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
     tot_dev, tot_wall = max_over_ranks([tot_dev, tot_wall], dist, "cuda")
     n_inst = per * args.steps * world
-    # roofline: one more pass over step 0's instances with every contraction launch
+    # roofline: one more pass over the timed instances with every contraction launch
     # bracketed by CUDA events on this stream (not part of the timed region)
     keys = ("prof_ms", "prof_bytes", "prof_ops", "prof_launches", "prof_stream_ms", "prof_stream_bytes",
             "prof_stream_launches", "prof_scount_ms", "prof_scount_bytes", "prof_scount_launches",
@@ -266,10 +267,12 @@ def run_ours(args, rank, world, local_rank):
     pb = {k: 0.0 for k in keys}
     if not args.no_profile_pass:
         prof = make_solver(profile=True)
-        for _, inst in instances(rank, world, 0, per):
-            r = prof.solve(inst, count=True, config=False)
-            for k in pb:
-                pb[k] += r.stats[k]
+        for s in range(args.steps):
+            P.clear_order_cache()
+            for _, inst in instances(rank, world, s, per):
+                r = prof.solve(inst, count=True, config=False)
+                for k in pb:
+                    pb[k] += r.stats[k]
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic()
 
@@ -347,6 +350,14 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": int(stats.get("launches", 0)),
         "tropical_gops": stats.get("tropical_ops", 0) / tot_dev / 1e9 if tot_dev else 0.0,
         "leaves_per_instance": stats.get("leaves", 0) / (per * args.steps),
+        # where an instance's time goes (library counters, per instance): host planning
+        # (branching, leaf plans and orders), host wall time waiting on leaf windows, and
+        # the device time of those windows
+        "time_split_ms": {k: 1000 * stats.get(s, 0) / (per * args.steps) for k, s in
+                          (("solve_wall", "t_total_s"), ("host_plan", "t_plan_s"), ("device_wait", "t_device_s"))}
+        | {"device_windows": stats.get("kernel_ms", 0) / (per * args.steps),
+           "kernels": pb["prof_ms"] / (per * args.steps) if not args.no_profile_pass else None},
+        "leaf_trials": args.leaf_trials,
         "plain_ttn": ttn,
         "roofline": dominant,
         "clocks": ck,
@@ -432,6 +443,8 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the per-launch roofline pass")
     ap.add_argument("--check", action="store_true", help="compare step 0 with the stored oracle answers")
+    ap.add_argument("--leaf-trials", type=int, default=0,
+                    help="annealing trials for the contraction order of each counting leaf (0: the root order)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not find the next instance's contraction order while the current one is solved")
     args = ap.parse_args()

@@ -65,6 +65,15 @@ const char *bbtn_last_error(void);
  * check prime used by the overflow guard). */
 int bbtn_primes(int n, uint64_t *primes);
 
+/* The first n pair moduli, written to moduli[0..n-1] (host): moduli[t] =
+ * q[2t+1] << 32 | q[2t] for the primes q = 2^30 - d, d ascending. A count plane
+ * with a pair modulus holds two residues per uint64 word: the low 32 bits mod
+ * q[2t], the high 32 bits mod q[2t+1] (each half below its prime). The solver's
+ * count planes take this form unless opts.wide_counts is set: a product of two
+ * words is then two 32 x 32-bit multiplies instead of one 64 x 64 -> 128-bit one.
+ * n <= BBTN_MAX_PRIMES + 1 (the last one is the check plane's). */
+int bbtn_prime_pairs(int n, uint64_t *moduli);
+
 /*
  * Chinese-remainder recombination (Garner's method) of k residues res[t] mod
  * distinct primes primes[t] (host arrays) into the unique integer in
@@ -88,8 +97,10 @@ int bbtn_crt_decimal(int k, const uint64_t *res, const uint64_t *primes, char *b
  * scalar (0, 1): a single-operand reduction.
  * va, vb, vc: device int32 value planes; ca, cb, cc: device uint64 count planes
  * (np planes each; unused when np == 0, the value-only mode). primes: host array of
- * np primes of the form 2^61 - c with c < 2^10 (as returned by bbtn_primes).
- * Input counts must already be reduced (< p_t). Output buffers must not alias
+ * np plane moduli, either all primes of the form 2^61 - c with c < 2^10 (as returned
+ * by bbtn_primes; one residue per word) or all pair moduli (as returned by
+ * bbtn_prime_pairs; two residues per word). Input counts must already be reduced
+ * (each residue below its prime). Output buffers must not alias
  * inputs. Ranks up to BBTN_MAX_RANK. Asynchronous on `stream`.
  */
 int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca,
@@ -178,7 +189,8 @@ typedef struct bbtn_ctx bbtn_ctx;   /* opaque; owned by the library */
 
 typedef struct {
     int space_cap_log2;      /* T_target of Eq. (4), in elements per tensor (default 24) */
-    int n_primes;            /* count residues, 0 (values only) .. BBTN_MAX_PRIMES (3) */
+    int n_primes;            /* count planes, 0 (values only) .. BBTN_MAX_PRIMES (3): 60 bits of
+                                degeneracy range each (61 with wide_counts) */
     uint64_t seed;           /* order finder / tie-breaking seed */
     int mode;                /* BBTN_MODE_* (default BBTN_MODE_BBTN) */
     int sa_iters;            /* simulated-annealing sweeps of the order finder (default 20) */
@@ -195,13 +207,16 @@ typedef struct {
                                 gamma (default 1: the one carrying the most overflow) */
     int leaf_trials;         /* BBTN counting leaves: order-finder trials (host threads) for each
                                 leaf's own contraction order, used when it fits the cap with less
-                                work than the root order restricted to the leaf (default 8; 0 =
-                                always the root order) */
+                                work than the root order restricted to the leaf (default 0: always
+                                the root order, which the min-fill root orders made as good on the
+                                30x30 King's-subgraph workload, at no host time) */
     int autotune;            /* time the register-tiled kernel's four load layouts on the first
                                 step of each shape class and keep the fastest for the context's
                                 later solves (default 0: the bit-0 rule, which the tuned choice
                                 matched on the 30x30 King's-subgraph workload) */
-    int reserved[3];
+    int wide_counts;         /* 1: one residue mod a prime 2^61 - c per count word; 0 (default): two
+                                residues mod primes 2^30 - d per word (bbtn_prime_pairs) */
+    int reserved[2];
 } bbtn_opts;
 
 typedef struct {
@@ -289,7 +304,8 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config);
 /* 2*H* for a spin glass (so that half-integer fields stay integral); alpha for MWIS. */
 int bbtn_get_energy(bbtn_ctx *ctx, int64_t *e);
 
-/* Count residues: res[t] = D mod primes[t], t < *k (host arrays of >= BBTN_MAX_PRIMES). */
+/* Count residues: res[t] = D mod primes[t], t < *k, one per CRT prime (two per count
+ * plane with pair moduli; host arrays of >= 2 * BBTN_MAX_PRIMES). */
 int bbtn_get_count_residues(bbtn_ctx *ctx, uint64_t *res, uint64_t *primes, int *k);
 
 /* Degeneracy D as a decimal string (CRT / Garner recombination of the residues).

@@ -44,6 +44,15 @@ def primes(n: int = 3):
     return [int(buf[i]) for i in range(n)]
 
 
+def prime_pairs(n: int = 3):
+    """The first n pair moduli q1 << 32 | q0 (primes q = 2^30 - d): a count plane with
+    such a modulus holds two residues per word, mod q0 (low half) and q1 (high half)."""
+    lib = _lib.load()
+    buf = (C.c_uint64 * max(n, 1))()
+    check(lib.bbtn_prime_pairs(n, buf))
+    return [int(buf[i]) for i in range(n)]
+
+
 def crt(residues, moduli) -> int:
     """The integer in [0, prod moduli) with the given residues (host Garner recombination)."""
     lib = _lib.load()
@@ -161,8 +170,8 @@ class Solver:
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
-                 profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 8, autotune: bool = False,
-                 stream=None, workspace=None):
+                 profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 0, autotune: bool = False,
+                 wide_counts: bool = False, stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
@@ -170,7 +179,7 @@ class Solver:
         o.sa_iters, o.region_size, o.batch, o.use_gnn = sa_iters, region_size, batch, int(use_gnn)
         o.count_check, o.use_symmetry = count_check, int(use_symmetry)
         o.max_slices_log2, o.profile, o.branch_lookahead = max_slices_log2, int(profile), branch_lookahead
-        o.leaf_trials, o.autotune = leaf_trials, int(autotune)
+        o.leaf_trials, o.autotune, o.wide_counts = leaf_trials, int(autotune), int(wide_counts)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:
@@ -262,7 +271,7 @@ class Solver:
         check(lib.bbtn_solve(self._ctx, int(count), int(config)))
         e = C.c_int64()
         check(lib.bbtn_get_energy(self._ctx, C.byref(e)))
-        res, prs, k = (C.c_uint64 * 8)(), (C.c_uint64 * 8)(), C.c_int()
+        res, prs, k = (C.c_uint64 * (2 * MAX_PRIMES))(), (C.c_uint64 * (2 * MAX_PRIMES))(), C.c_int()
         check(lib.bbtn_get_count_residues(self._ctx, res, prs, C.byref(k)))
         cnt = None
         if count:

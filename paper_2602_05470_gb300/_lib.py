@@ -31,7 +31,7 @@ class Opts(C.Structure):
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
                 ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("leaf_trials", C.c_int),
-                ("autotune", C.c_int), ("reserved", C.c_int * 3)]
+                ("autotune", C.c_int), ("wide_counts", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class Stats(C.Structure):
@@ -72,6 +72,7 @@ _SIGS = {
     "bbtn_version": ([], C.c_char_p),
     "bbtn_last_error": ([], C.c_char_p),
     "bbtn_primes": ([C.c_int, _u64p], C.c_int),
+    "bbtn_prime_pairs": ([C.c_int, _u64p], C.c_int),
     "bbtn_crt_decimal": ([C.c_int, _u64p, _u64p, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_contract": ([C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp,
                        C.c_int, _u64p, _vp], C.c_int),

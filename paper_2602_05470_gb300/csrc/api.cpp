@@ -65,16 +65,7 @@ int find(int r, const int32_t *l, int x) {
     return -1;
 }
 
-void cprimes_from(int np, const uint64_t *primes, uint32_t *c) {
-    if (np < 0 || np > kMaxPlanes) fail(BBTN_EINVAL, "np out of range");
-    if (np > 0 && !primes) fail(BBTN_EINVAL, "primes missing");
-    for (int t = 0; t < np; t++) {
-        uint64_t cc = (1ull << 61) - primes[t];
-        if (primes[t] >= (1ull << 61) || cc >= 1024 || !is_prime_u64(primes[t]))
-            fail(BBTN_EINVAL, "primes must be primes 2^61 - c with c < 1024");
-        c[t] = (uint32_t)cc;
-    }
-}
+void cprimes_from(int np, const uint64_t *primes, uint32_t *c) { plane_moduli(np, primes, c); }
 
 }  // namespace
 
@@ -89,6 +80,14 @@ int bbtn_primes(int n, uint64_t *primes) {
         const auto &tab = prime_table();
         if (n < 0 || n > (int)tab.size() || (n > 0 && !primes)) fail(BBTN_EINVAL, "bad prime count");
         for (int i = 0; i < n; i++) primes[i] = tab[i];
+    });
+}
+
+int bbtn_prime_pairs(int n, uint64_t *moduli) {
+    return guarded([&] {
+        const auto &tab = pair_prime_table();
+        if (n < 0 || 2 * n > (int)tab.size() || (n > 0 && !moduli)) fail(BBTN_EINVAL, "bad pair count");
+        for (int i = 0; i < n; i++) moduli[i] = tab[2 * i + 1] << 32 | tab[2 * i];
     });
 }
 
@@ -282,8 +281,9 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->profile = 0;
     o->max_slices_log2 = 30;
     o->branch_lookahead = 1;
-    o->leaf_trials = 8;
+    o->leaf_trials = 0;
     o->autotune = 0;
+    o->wide_counts = 0;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -407,11 +407,12 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         ctx->out = s.solve(ctx->prob, want_count != 0, want_config != 0, &ctx->stats);
         ctx->solved = true;
         if (ctx->out.checked) {
+            // the residues after the CRT ones are those of the check plane
             std::vector<uint64_t> r(ctx->out.res.begin(), ctx->out.res.begin() + ctx->out.n_crt);
             std::vector<uint64_t> p(ctx->out.primes.begin(), ctx->out.primes.begin() + ctx->out.n_crt);
-            const uint64_t q = ctx->out.primes.back();
-            if (crt_mod(r, p, q) != ctx->out.res.back())
-                fail(BBTN_EOVERFLOW, "degeneracy exceeds the range of the CRT primes; use more primes");
+            for (size_t u = ctx->out.n_crt; u < ctx->out.res.size(); u++)
+                if (crt_mod(r, p, ctx->out.primes[u]) != ctx->out.res[u])
+                    fail(BBTN_EOVERFLOW, "degeneracy exceeds the range of the CRT primes; use more primes");
         }
     });
 }

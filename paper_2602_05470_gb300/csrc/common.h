@@ -41,7 +41,14 @@ inline double now_s() {
 // Index kCheckPrime is reserved for the overflow guard.
 constexpr int kCheckPrime = BBTN_MAX_PRIMES;
 const std::vector<uint64_t> &prime_table();     // BBTN_MAX_PRIMES + 1 entries
+// Primes q = 2^30 - d (d ascending, d < 2^10) for count planes that hold two residues:
+// plane t of the pair form takes q[2t] (low half) and q[2t + 1] (high half), and the
+// check plane q[2 kCheckPrime], q[2 kCheckPrime + 1].
+const std::vector<uint64_t> &pair_prime_table();   // 2 (BBTN_MAX_PRIMES + 1) entries
 bool is_prime_u64(uint64_t n);
+// Checks np plane moduli (all primes 2^61 - c, or all pairs q1 << 32 | q0 of primes
+// 2^30 - d) and writes each plane's constant word for the kernels; fails on others.
+void plane_moduli(int np, const uint64_t *primes, uint32_t *c);
 
 // Garner recombination of residues r[t] mod p[t] into a decimal string.
 std::string crt_decimal(const std::vector<uint64_t> &r, const std::vector<uint64_t> &p);

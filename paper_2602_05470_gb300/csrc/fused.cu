@@ -81,13 +81,13 @@ __global__ void __launch_bounds__(kThr) k_fused(const __grid_constant__ FusedPar
 #pragma unroll
                         for (int t = 0; t < NP; t++) {
                             const uint32_t c = p.cprime[t];
-                            const uint64_t x = ac ? ac[(uint64_t)t * aplane + ea] : 1ull;
-                            const uint64_t y = bc ? bc[(uint64_t)t * bplane + eb] : 1ull;
+                            const uint64_t x = ac ? ac[(uint64_t)t * aplane + ea] : count_one(c);
+                            const uint64_t y = bc ? bc[(uint64_t)t * bplane + eb] : count_one(c);
                             uint64_t term;
                             if (!ac) term = y;
                             else if (!bc) term = x;
-                            else term = mulmod61(x, y, c);
-                            acc[t] = addmod61(acc[t], term, c);
+                            else term = cmul(x, y, c);
+                            acc[t] = cadd(acc[t], term, c);
                         }
                     }
                 }

@@ -28,12 +28,6 @@ __device__ __forceinline__ uint64_t tab4(const uint32_t (*t)[256], uint64_t o) {
            t[3][(o >> 24) & 255];
 }
 
-template <int NP>
-__device__ __forceinline__ uint64_t count_of(const Operand &X, int t, uint64_t e, int32_t v) {
-    if (X.unit_counts) return v >= kFiniteMin ? 1ull : 0ull;
-    return X.cnt[(uint64_t)t * X.plane + e];
-}
-
 // ----------------------------------------------------------------------------- K1/K3
 template <int NP, bool HASB>
 __global__ void __launch_bounds__(kThreads)
@@ -130,13 +124,14 @@ k_contract(const __grid_constant__ ContractParams P) {
                             const uint32_t c = P.cprime[t];
                             uint64_t term;
                             if (P.A.unit_counts) {
-                                term = HASB ? (P.B.unit_counts ? 1ull : __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb)) : 1ull;
+                                term = HASB ? (P.B.unit_counts ? count_one(c) : __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb))
+                                            : count_one(c);
                             } else {
                                 const uint64_t x = __ldg(P.A.cnt + (uint64_t)t * P.A.plane + ea);
                                 if (!HASB || P.B.unit_counts) term = x;
-                                else term = mulmod61(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb), c);
+                                else term = cmul(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb), c);
                             }
-                            acc[t] = addmod61(acc[t], term, c);
+                            acc[t] = cadd(acc[t], term, c);
                         }
                     }
                 }
@@ -255,7 +250,7 @@ __device__ __forceinline__ void acc_merge(Acc<NP> &x, const Acc<NP> &y, const ui
         x = y;
     } else if (y.v == x.v) {
 #pragma unroll
-        for (int t = 0; t < NP; t++) x.c[t] = addmod61(x.c[t], y.c[t], cp[t]);
+        for (int t = 0; t < NP; t++) x.c[t] = cadd(x.c[t], y.c[t], cp[t]);
     }
 }
 

@@ -61,13 +61,7 @@ extern "C" int bbtn_aggregate_noalloc(int64_t n, const int32_t *vals, const uint
             fail(BBTN_EINVAL, "bad aggregate arguments");
         if (np < 0 || np > kMaxPlanes) fail(BBTN_EINVAL, "np out of range");
         uint32_t c[kMaxPlanes] = {0};
-        for (int t = 0; t < np; t++) {
-            if (!primes) fail(BBTN_EINVAL, "primes missing");
-            const uint64_t cc = (1ull << 61) - primes[t];
-            if (primes[t] >= (1ull << 61) || cc >= 1024 || !is_prime_u64(primes[t]))
-                fail(BBTN_EINVAL, "primes must be primes 2^61 - c with c < 1024");
-            c[t] = (uint32_t)cc;
-        }
+        plane_moduli(np, primes, c);
         const size_t need = aggregate_scratch_bytes(n, np);
         if (need > kNoAllocScratchBytes)
             fail(BBTN_EINVAL, "reduction needs " + std::to_string(need) + " scratch bytes, more than the fixed " +

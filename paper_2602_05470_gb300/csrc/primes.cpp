@@ -3,6 +3,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "semiring.cuh"
 
 namespace bbtn {
 
@@ -61,6 +62,41 @@ const std::vector<uint64_t> &prime_table() {
         }
     });
     return tab;
+}
+
+const std::vector<uint64_t> &pair_prime_table() {
+    static std::vector<uint64_t> tab;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint64_t d = 1; tab.size() < 2 * ((size_t)BBTN_MAX_PRIMES + 1) && d < 1024; d++) {
+            uint64_t q = (1ull << 30) - d;
+            if (is_prime_u64(q)) tab.push_back(q);
+        }
+    });
+    return tab;
+}
+
+// A plane's modulus word: a prime 2^61 - c (one residue per word), or a pair
+// q1 << 32 | q0 of distinct primes 2^30 - d (two residues per word); every plane of
+// one call takes the same form.
+void plane_moduli(int np, const uint64_t *primes, uint32_t *c) {
+    if (np < 0 || np > kMaxPlanes) fail(BBTN_EINVAL, "np out of range");
+    if (np > 0 && !primes) fail(BBTN_EINVAL, "primes missing");
+    auto small = [](uint64_t q) { return q < (1ull << 30) && (1ull << 30) - q < 1024 && is_prime_u64(q); };
+    for (int t = 0; t < np; t++) {
+        const uint64_t m = primes[t];
+        if (m >= (1ull << 61)) {
+            const uint64_t q0 = m & 0xffffffffull, q1 = m >> 32;
+            if (!small(q0) || !small(q1) || q0 == q1)
+                fail(BBTN_EINVAL, "a pair modulus must be q1 << 32 | q0, distinct primes 2^30 - d with d < 1024");
+            c[t] = kPairFlag | (uint32_t)((1ull << 30) - q0) | (uint32_t)((1ull << 30) - q1) << 10;
+        } else {
+            uint64_t cc = (1ull << 61) - m;
+            if (cc >= 1024 || !is_prime_u64(m)) fail(BBTN_EINVAL, "primes must be primes 2^61 - c with c < 1024");
+            c[t] = (uint32_t)cc;
+        }
+        if (is_pair(c[t]) != is_pair(c[0])) fail(BBTN_EINVAL, "all count planes of a call take the same modulus form");
+    }
 }
 
 namespace {

@@ -6,7 +6,14 @@
 // the max-plus network of the negated energies, so
 //   (a, c) (+) (b, d) = (max(a, b), c + d if a == b else the count of the larger)
 //   (a, c) (x) (b, d) = (a + b, c * d)
-// Counts are residues modulo primes p = 2^61 - c with c < 2^10.
+// Counts are residues in 64-bit words, one word per count plane, in one of two forms:
+//  - wide: one residue modulo a prime p = 2^61 - c with c < 2^10;
+//  - pair: two residues, the low 32 bits modulo q0 = 2^30 - d0 and the high 32 bits
+//    modulo q1 = 2^30 - d1 (d0, d1 < 2^10). A product of two pair residues is two
+//    32 x 32 -> 64-bit multiplies, and sixteen of them sum without overflow, where a
+//    wide product needs a 64 x 64 -> 128-bit multiply.
+// A plane's form and constants travel in one 32-bit word `c`: c < 2^10 is the wide
+// prime's c; c = kPairFlag | d0 | d1 << 10 is a pair.
 #pragma once
 #include <stdint.h>
 
@@ -51,6 +58,49 @@ __host__ __device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b, ui
     const uint64_t p = (1ull << 61) - c;
     uint64_t s = a + b;                // < 2^62, no wrap
     return s >= p ? s - p : s;
+}
+
+constexpr uint32_t kPairFlag = 1u << 31;
+constexpr uint64_t kM30 = (1ull << 30) - 1;
+
+__host__ __device__ __forceinline__ bool is_pair(uint32_t c) { return (c & kPairFlag) != 0; }
+__host__ __device__ __forceinline__ uint32_t pair_d0(uint32_t c) { return c & 1023u; }
+__host__ __device__ __forceinline__ uint32_t pair_d1(uint32_t c) { return (c >> 10) & 1023u; }
+
+// x mod q for q = 2^30 - d, d < 2^10, any x < 2^64: 2^30 == d (mod q), so
+// x = h 2^30 + l == h d + l; h < 2^34 gives y < 2^44 + 2^30, and folding y once more
+// gives z < 2^30 + 2^25 < 2q, fixed by one conditional subtraction.
+__host__ __device__ __forceinline__ uint32_t reduce64_30(uint64_t x, uint32_t d) {
+    const uint64_t y = (x >> 30) * d + (x & kM30);
+    const uint32_t z = (uint32_t)(y >> 30) * d + (uint32_t)(y & kM30);
+    const uint32_t q = (1u << 30) - d;
+    return z >= q ? z - q : z;
+}
+
+__host__ __device__ __forceinline__ uint64_t mulmod_pair(uint64_t a, uint64_t b, uint32_t c) {
+    const uint32_t lo = reduce64_30((uint64_t)(uint32_t)a * (uint32_t)b, pair_d0(c));
+    const uint32_t hi = reduce64_30((a >> 32) * (b >> 32), pair_d1(c));
+    return (uint64_t)hi << 32 | lo;
+}
+
+// both halves below 2^30, so their sums do not carry into each other
+__host__ __device__ __forceinline__ uint64_t addmod_pair(uint64_t a, uint64_t b, uint32_t c) {
+    uint64_t s = a + b;
+    const uint32_t q0 = (1u << 30) - pair_d0(c), q1 = (1u << 30) - pair_d1(c);
+    if ((uint32_t)s >= q0) s -= q0;
+    if ((uint32_t)(s >> 32) >= q1) s -= (uint64_t)q1 << 32;
+    return s;
+}
+
+// the count 1 of a plane, and the semiring product / sum of two residue words
+__host__ __device__ __forceinline__ uint64_t count_one(uint32_t c) { return is_pair(c) ? 0x100000001ull : 1ull; }
+
+__host__ __device__ __forceinline__ uint64_t cmul(uint64_t a, uint64_t b, uint32_t c) {
+    return is_pair(c) ? mulmod_pair(a, b, c) : mulmod61(a, b, c);
+}
+
+__host__ __device__ __forceinline__ uint64_t cadd(uint64_t a, uint64_t b, uint32_t c) {
+    return is_pair(c) ? addmod_pair(a, b, c) : addmod61(a, b, c);
 }
 
 }  // namespace bbtn

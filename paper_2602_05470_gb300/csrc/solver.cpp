@@ -464,19 +464,33 @@ void Solver::setup(const Problem &p, bool want_count) {
 
 void Solver::setup_host(const Problem &p, bool want_count) {
     p_ = &p;
-    const auto &tab = prime_table();
     n_crt_ = want_count ? std::max(0, std::min(opts_.n_primes, BBTN_MAX_PRIMES)) : 0;
     if (want_count && n_crt_ == 0) n_crt_ = 1;
+    // count planes: by default two residues per word (primes 2^30 - d, 60 bits of range
+    // a plane), else one (2^61 - c, 61 bits)
+    pair_ = opts_.wide_counts == 0;
+    const int bits = pair_ ? 60 : 61;
     check_ = false;
     if (n_crt_ > 0) {
         if (opts_.count_check == 1) check_ = true;
-        else if (opts_.count_check < 0) check_ = p.n + 1 > 61 * n_crt_ - 2;   // D <= 2^n
+        else if (opts_.count_check < 0) check_ = p.n + 1 > bits * n_crt_ - 2;   // D <= 2^n
     }
     np_ = n_crt_ + (check_ ? 1 : 0);
     primes_.clear();
-    for (int t = 0; t < n_crt_; t++) primes_.push_back(tab[t]);
-    if (check_) primes_.push_back(tab[kCheckPrime]);
-    for (int t = 0; t < np_; t++) cprime_[t] = (uint32_t)((1ull << 61) - primes_[t]);
+    if (pair_) {
+        const auto &tab = pair_prime_table();
+        for (int t = 0; t < np_; t++) {
+            const int i = t < n_crt_ ? t : kCheckPrime;
+            primes_.push_back(tab[2 * i]);
+            primes_.push_back(tab[2 * i + 1]);
+            cprime_[t] = kPairFlag | (uint32_t)((1ull << 30) - tab[2 * i]) | (uint32_t)((1ull << 30) - tab[2 * i + 1]) << 10;
+        }
+    } else {
+        const auto &tab = prime_table();
+        for (int t = 0; t < n_crt_; t++) primes_.push_back(tab[t]);
+        if (check_) primes_.push_back(tab[kCheckPrime]);
+        for (int t = 0; t < np_; t++) cprime_[t] = (uint32_t)((1ull << 61) - primes_[t]);
+    }
 
     fx0_.assign(p.n, -1);
     mult_ = 1;
@@ -1012,10 +1026,18 @@ void Solver::finish(bool want_config) {
     BBTN_CUDA(cudaStreamSynchronize(stream_));
     if (v < kFiniteMin) fail(BBTN_ESTATE, "no feasible configuration");
     out_.value = v;
-    for (int t = 0; t < np_; t++) r[t] = mulmod_host(r[t], mult_ % primes_[t], primes_[t]);
+    if (pair_) {   // one residue per modulus: low half, then high half of each plane
+        std::vector<uint64_t> u;
+        for (int t = 0; t < np_; t++) {
+            u.push_back(r[t] & 0xffffffffull);
+            u.push_back(r[t] >> 32);
+        }
+        r.swap(u);
+    }
+    for (size_t t = 0; t < r.size(); t++) r[t] = mulmod_host(r[t], mult_ % primes_[t], primes_[t]);
     out_.res = r;
     out_.primes = primes_;
-    out_.n_crt = n_crt_;
+    out_.n_crt = pair_ ? 2 * n_crt_ : n_crt_;
     out_.checked = check_;
     if (want_config) {
         if (best_fx_.empty() || best_val_ != v) fail(BBTN_ESTATE, "optimal branch not recorded");

@@ -20,10 +20,10 @@ void clear_order_cache();
 
 struct SolveOutput {
     int64_t value = 0;                 // max-plus value of the network (-2H* or alpha)
-    std::vector<uint64_t> res;         // residues (CRT primes first, check prime last if used)
-    std::vector<uint64_t> primes;
+    std::vector<uint64_t> res;         // one residue per modulus: the CRT ones, then the check plane's
+    std::vector<uint64_t> primes;      // the moduli, in the same order
     int n_crt = 0;                     // residues that enter the CRT
-    bool checked = false;              // last residue is the overflow check
+    bool checked = false;              // the residues after the first n_crt are the overflow check
     std::vector<int8_t> x;             // optimal configuration (0/1 per variable)
     bool have_x = false;
 };
@@ -98,6 +98,7 @@ class Solver {
     CTree tree_;                        // reference tree (labels of the free network)
     std::vector<int8_t> fx0_;           // root fixed variables (symmetry)
     int np_ = 0, n_crt_ = 0;
+    bool pair_ = true;                  // count planes hold two residues mod 30-bit primes
     bool check_ = false;
     std::vector<uint64_t> primes_;
     uint32_t cprime_[kMaxPlanes] = {0};

@@ -30,7 +30,7 @@ __device__ __forceinline__ void merge(Part<NP> &x, const Part<NP> &y, const uint
         x = y;
     } else if (y.v == x.v) {
 #pragma unroll
-        for (int t = 0; t < NP; t++) x.c[t] = addmod61(x.c[t], y.c[t], cp[t]);
+        for (int t = 0; t < NP; t++) x.c[t] = cadd(x.c[t], y.c[t], cp[t]);
     }
 }
 
@@ -115,9 +115,10 @@ __global__ void __launch_bounds__(kThr) k_splitk(const __grid_constant__ Contrac
 #pragma unroll
         for (int t = 0; t < NP; t++) {
             if (!fin) { y.c[t] = 0; continue; }
-            const uint64_t x = P.A.unit_counts ? 1ull : __ldg(P.A.cnt + (uint64_t)t * P.A.plane + ea);
-            const uint64_t z = (!HASB || P.B.unit_counts) ? 1ull : __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb);
-            y.c[t] = (P.A.unit_counts || !HASB || P.B.unit_counts) ? (x * z) : mulmod61(x, z, P.cprime[t]);
+            const uint32_t c = P.cprime[t];
+            const uint64_t x = P.A.unit_counts ? count_one(c) : __ldg(P.A.cnt + (uint64_t)t * P.A.plane + ea);
+            const uint64_t z = (!HASB || P.B.unit_counts) ? count_one(c) : __ldg(P.B.cnt + (uint64_t)t * P.B.plane + eb);
+            y.c[t] = P.A.unit_counts ? z : (!HASB || P.B.unit_counts) ? x : cmul(x, z, c);
         }
         merge<NP>(acc, y, P.cprime);
     }

@@ -181,13 +181,13 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
                             if (P.A.unit_counts) {
                                 term = (HASB && !P.B.unit_counts)
                                            ? __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j])
-                                           : 1ull;
+                                           : count_one(c);
                             } else {
                                 const uint64_t x = __ldg(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ej);
                                 if (!HASB || P.B.unit_counts) term = x;
-                                else term = mulmod61(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
+                                else term = cmul(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
                             }
-                            acc[j][t] = addmod61(acc[j][t], term, c);
+                            acc[j][t] = cadd(acc[j][t], term, c);
                         }
                     }
                 }

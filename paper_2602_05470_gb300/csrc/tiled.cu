@@ -73,7 +73,7 @@ __device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32
 __device__ __forceinline__ uint32_t chunk_off(const uint32_t *koff, int k0) { return kof(koff, (uint32_t)k0); }
 
 // load one chunk of values (and counts) into shared memory as [k][m]
-template <int NP, int ROWS, int R>
+template <int NP, bool PR, int ROWS, int R>
 __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
                                           uint64_t plane, int unit, const Lanes<R> &L, uint32_t kb,
                                           int32_t *sv, uint64_t *sc) {
@@ -86,7 +86,7 @@ __device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const u
 #pragma unroll
             for (int t = 0; t < NP; t++)
                 sc[t * TK * (ROWS + 2) + (L.sidx[r] / (ROWS + 4)) * (ROWS + 2) + L.sidx[r] % (ROWS + 4)] =
-                    unit ? (x >= kFiniteMin ? 1ull : 0ull) : __ldg(c + (uint64_t)t * plane + off);
+                    unit ? (x >= kFiniteMin ? (PR ? 0x100000001ull : 1ull) : 0ull) : __ldg(c + (uint64_t)t * plane + off);
         }
     }
 }
@@ -98,7 +98,7 @@ constexpr int32_t kFinite16 = -(1 << 13);
 __device__ __forceinline__ int32_t to16(int32_t x) { return x >= kFiniteMin ? x : kNeg16; }
 __device__ __forceinline__ uint32_t dup16(int32_t x) { return ((uint32_t)x & 0xffffu) | ((uint32_t)x << 16); }
 
-template <int NP, bool V16, int TN>
+template <int NP, bool V16, int TN, bool PR>
 __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups &G, int fastA_k, int fastB_k,
                                            uint64_t tile, unsigned char *smem_raw) {
     // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
@@ -270,8 +270,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                 for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
         for (int k0 = 0; k0 < K; k0 += TK) {
-            load_tile<NP, TM, 4>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], &cA[0][0][0]);
-            load_tile<NP, TN, RB>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], &cB[0][0][0]);
+            load_tile<NP, PR, TM, 4>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], &cA[0][0][0]);
+            load_tile<NP, PR, TN, RB>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], &cB[0][0][0]);
             __syncthreads();
             int32_t cm[4][MC];
 #pragma unroll
@@ -304,18 +304,42 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                         for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
                     }
                     if (cm[i][j] == best[i][j] && cm[i][j] >= kFiniteMin) {
-                        u128 part[NP];
-#pragma unroll
-                        for (int t = 0; t < NP; t++) part[t] = 0;
                         const int mi = ty * 4 + i, nj = tx * MC + j;
-                        for (int kk = 0; kk < TK; kk++) {
-                            if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+                        if constexpr (PR) {
+                            // two residues per word: each half's products are below 2^60,
+                            // so the chunk's (at most 16) terms sum in 64 bits exactly
+                            uint64_t s0[NP], s1[NP];
 #pragma unroll
-                            for (int t = 0; t < NP; t++) part[t] += (u128)cA[t][kk][mi] * cB[t][kk][nj];
+                            for (int t = 0; t < NP; t++) s0[t] = s1[t] = 0;
+                            for (int kk = 0; kk < TK; kk++) {
+                                if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+#pragma unroll
+                                for (int t = 0; t < NP; t++) {
+                                    const uint64_t x = cA[t][kk][mi], y = cB[t][kk][nj];
+                                    s0[t] += (uint64_t)(uint32_t)x * (uint32_t)y;
+                                    s1[t] += (uint64_t)(uint32_t)(x >> 32) * (uint32_t)(y >> 32);
+                                }
+                            }
+#pragma unroll
+                            for (int t = 0; t < NP; t++) {
+                                const uint32_t c = P.cprime[t];
+                                const uint64_t w = (uint64_t)reduce64_30(s1[t], pair_d1(c)) << 32 |
+                                                   reduce64_30(s0[t], pair_d0(c));
+                                acc[i][j][t] = addmod_pair(acc[i][j][t], w, c);
+                            }
+                        } else {
+                            u128 part[NP];
+#pragma unroll
+                            for (int t = 0; t < NP; t++) part[t] = 0;
+                            for (int kk = 0; kk < TK; kk++) {
+                                if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+#pragma unroll
+                                for (int t = 0; t < NP; t++) part[t] += (u128)cA[t][kk][mi] * cB[t][kk][nj];
+                            }
+#pragma unroll
+                            for (int t = 0; t < NP; t++)
+                                acc[i][j][t] = addmod61(acc[i][j][t], reduce128_61(part[t], P.cprime[t]), P.cprime[t]);
                         }
-#pragma unroll
-                        for (int t = 0; t < NP; t++)
-                            acc[i][j][t] = addmod61(acc[i][j][t], reduce128_61(part[t], P.cprime[t]), P.cprime[t]);
                     }
                 }
             __syncthreads();
@@ -344,11 +368,11 @@ struct TArgs {
     Groups g[NB];
 };
 
-template <int NP, int NB, bool V16, int TNC>
+template <int NP, int NB, bool V16, int TNC, bool PR>
 __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
-        tiled_body<NP, V16, TNC>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
+        tiled_body<NP, V16, TNC, PR>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
     } else {
         __shared__ ContractParams sP;
         __shared__ Groups sG;
@@ -359,7 +383,7 @@ __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_co
         const unsigned char *gsrc = (const unsigned char *)&args.g[e];
         for (int i = threadIdx.x; i < (int)sizeof(Groups); i += blockDim.x) ((unsigned char *)&sG)[i] = gsrc[i];
         __syncthreads();
-        tiled_body<NP, V16, TNC>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
+        tiled_body<NP, V16, TNC, PR>(sP, sG, args.fa[e], args.fb[e], blockIdx.x - args.blk0[e], smem_raw);
     }
 }
 
@@ -372,7 +396,7 @@ size_t tiled_smem(int np, int tn) {
 // column tile of a step: 64 when its B-only group has at least 6 labels, else 16
 inline int column_tile(const Groups &g) { return g.nn >= 6 ? 64 : 16; }
 
-template <int NP, int NB, bool V16, int TNC>
+template <int NP, int NB, bool V16, int TNC, bool PR>
 cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, const int *fb, int n, cudaStream_t s) {
     TArgs<NB> a;
     memset(&a, 0, sizeof a);
@@ -390,10 +414,10 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
     }
     a.blk0[n] = (uint32_t)total;
     const size_t smem = tiled_smem(NP, TNC);
-    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16, TNC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16, TNC, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_tiled<NP, NB, V16, TNC><<<(unsigned)total, kThr, smem, s>>>(a);
+    k_tiled<NP, NB, V16, TNC, PR><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -432,14 +456,19 @@ bool make_groups(const ContractParams &p, Groups &g, int &fa, int &fb) {
 template <int NB, int TNC>
 cudaError_t dispatch_t(const ContractParams *p, const Groups *g, const int *fa, const int *fb, int n, cudaStream_t s) {
     const bool v16 = TNC == 64 && p[0].v16;
+    const bool pr = p[0].np > 0 && is_pair(p[0].cprime[0]);
+#define BBTN_TILED_NP(N) \
+    case N: return pr ? launch_t<N, NB, false, TNC, true>(p, g, fa, fb, n, s) : launch_t<N, NB, false, TNC, false>(p, g, fa, fb, n, s);
     switch (p[0].np) {
-        case 0: return v16 ? launch_t<0, NB, true, 64>(p, g, fa, fb, n, s) : launch_t<0, NB, false, TNC>(p, g, fa, fb, n, s);
-        case 1: return launch_t<1, NB, false, TNC>(p, g, fa, fb, n, s);
-        case 2: return launch_t<2, NB, false, TNC>(p, g, fa, fb, n, s);
-        case 3: return launch_t<3, NB, false, TNC>(p, g, fa, fb, n, s);
-        case 4: return launch_t<4, NB, false, TNC>(p, g, fa, fb, n, s);
+        case 0: return v16 ? launch_t<0, NB, true, 64, false>(p, g, fa, fb, n, s)
+                           : launch_t<0, NB, false, TNC, false>(p, g, fa, fb, n, s);
+        BBTN_TILED_NP(1)
+        BBTN_TILED_NP(2)
+        BBTN_TILED_NP(3)
+        BBTN_TILED_NP(4)
         default: return cudaErrorNotSupported;
     }
+#undef BBTN_TILED_NP
 }
 
 // entries with 64- and 16-wide column tiles go out in separate launches
@@ -497,7 +526,8 @@ cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStre
     Groups g[kBatchMax];
     int fa[kBatchMax], fb[kBatchMax];
     for (int i = 0; i < n; i++) {
-        if (p[i].np != p[0].np || p[i].v16 != p[0].v16 || !make_groups(p[i], g[i], fa[i], fb[i]))
+        if (p[i].np != p[0].np || p[i].v16 != p[0].v16 ||
+            (p[i].np > 0 && is_pair(p[i].cprime[0]) != is_pair(p[0].cprime[0])) || !make_groups(p[i], g[i], fa[i], fb[i]))
             return cudaErrorNotSupported;
         if (lanes >= 0) {   // the caller's (an autotuner's) choice instead of the bit-0 rule
             fa[i] = lanes & 1;

@@ -377,3 +377,104 @@ def test_contract_values16(P, case):
     assert feas.any() and (~feas).any()
     assert np.array_equal(got[feas], ov[feas])
     assert (got[~feas] < -(1 << 28)).all()
+
+
+# ---- count planes with pair moduli: two residues per word, mod primes 2^30 - d.
+# The oracle contracts the low halves mod q0 and the high halves mod q1 separately.
+M32 = np.uint64(0xFFFFFFFF)
+
+
+def _pair_planes(rng, v, moduli):
+    planes = []
+    for m in moduli:
+        q0, q1 = m & 0xFFFFFFFF, m >> 32
+        lo = rng.integers(0, q0, size=v.size, dtype=np.uint64)
+        hi = rng.integers(0, q1, size=v.size, dtype=np.uint64)
+        w = lo | (hi << np.uint64(32))
+        w[v < -(1 << 28)] = 0
+        planes.append(w)
+    return np.stack(planes) if planes else np.zeros((0, v.size), np.uint64)
+
+
+def _oracle_pair(la, va, ca, lb, vb, cb, lc, moduli):
+    q0 = [m & 0xFFFFFFFF for m in moduli]
+    q1 = [m >> 32 for m in moduli]
+    half = lambda c, s: None if c is None else (c >> np.uint64(s)) & M32
+    ov, lo = oracle.contract(la, va, half(ca, 0), lb, vb, half(cb, 0), lc, q0)
+    _, hi = oracle.contract(la, va, half(ca, 32), lb, vb, half(cb, 32), lc, q1)
+    return ov, lo | (hi << np.uint64(32))
+
+
+def _pair_case(P, la, lb, lc, np_, seed, lo=-3, hi=3, neg=0.05, unitA=False, unitB=False):
+    rng = np.random.default_rng(seed)
+    moduli = P.prime_pairs(np_)
+    va = rng.integers(lo, hi + 1, size=1 << len(la)).astype(np.int32)
+    va[rng.random(va.size) < neg] = oracle.NEG
+    ca = _pair_planes(rng, va, moduli)
+    vb = cb = None
+    if lb is not None:
+        vb = rng.integers(lo, hi + 1, size=1 << len(lb)).astype(np.int32)
+        vb[rng.random(vb.size) < neg] = oracle.NEG
+        cb = _pair_planes(rng, vb, moduli)
+    one = np.uint64(0x100000001)
+    if unitA:
+        ca = np.where(va >= -(1 << 28), one, np.uint64(0))[None, :].repeat(np_, 0)
+    if unitB and lb is not None:
+        cb = np.where(vb >= -(1 << 28), one, np.uint64(0))[None, :].repeat(np_, 0)
+    vc, cc = _run(P, la, (va, ca), lb, None if lb is None else (vb, cb), lc, moduli, unitA=unitA, unitB=unitB)
+    ov, oc = _oracle_pair(la, va, ca, lb, vb, cb, lc, moduli)
+    assert np.array_equal(vc, ov)
+    assert np.array_equal(cc, oc)
+
+
+PAIR_CASES = ([CASES[i] for i in (0, 3, 6, 7, 8, 9)] + [_tiled_case(*t) for t in TILED] +
+              [(la, lb, lc) for la, lb, lc in SPLITK] + [(la, lb, lc) for la, lb, lc, _, _ in VEC[:7]])
+
+
+@pytest.mark.parametrize("case", range(len(PAIR_CASES)))
+@pytest.mark.parametrize("np_", [1, 4])
+def test_contract_pair_moduli(P, case, np_):
+    """Every kernel family (streaming, four-outputs streaming, register-tiled 64- and
+    16-wide, split-K, reductions) with pair-modulus count planes."""
+    la, lb, lc = PAIR_CASES[case]
+    _pair_case(P, la, lb, lc, np_, 1300 + case, lo=-4, hi=4)
+
+
+@pytest.mark.parametrize("case", [0, 8, 12, 13])
+def test_contract_pair_unit_counts(P, case):
+    """Unit counts (implied by the values) enter as 1 in both halves of the word."""
+    la, lb, lc = PAIR_CASES[case]
+    _pair_case(P, la, lb, lc, 3, 1400 + case, unitA=True, unitB=case % 2 == 0)
+
+
+def test_contract_pair_dense_ties(P):
+    """All values equal: every summed assignment ties, so a tiled chunk adds 16
+    products per output half (the most its 64-bit sums take before reduction)."""
+    la, lb, lc = _tiled_case(6, 6, 8, 1, "k", "n", "mnb")
+    _pair_case(P, la, lb, lc, 4, 1500, lo=0, hi=0, neg=0.0)
+
+
+def test_contract_pair_rejects_mixed_moduli(P):
+    la, lb, lc = CASES[0]
+    rng = np.random.default_rng(1)
+    v = rng.integers(-2, 3, size=16).astype(np.int32)
+    c = np.zeros((2, 16), np.uint64)
+    with pytest.raises(P.BBTNError):
+        _run(P, la, (v, c), lb, (v, c), lc, [P.primes(1)[0], P.prime_pairs(1)[0]])
+
+
+@pytest.mark.parametrize("n", [1, 257, 70000])
+def test_aggregate_pair_moduli(P, n):
+    rng = np.random.default_rng(77 + n)
+    moduli = P.prime_pairs(3)
+    v = rng.integers(-2, 1, size=n).astype(np.int32)
+    c = _pair_planes(rng, v, moduli)
+    ov_, oc_ = P.aggregate(torch.from_numpy(v).cuda(), torch.from_numpy(c.view(np.int64).copy()).cuda(), moduli)
+    torch.cuda.synchronize()
+    r = max(0, int(np.ceil(np.log2(max(n, 1)))))
+    pv = np.full(1 << r, oracle.NEG, np.int32)
+    pc = np.zeros((3, 1 << r), np.uint64)
+    pv[:n], pc[:, :n] = v, c
+    ev, ec = _oracle_pair(list(range(r)), pv, pc, None, None, None, [], moduli)
+    assert int(ov_.cpu()[0]) == int(ev[0])
+    assert np.array_equal(oc_.cpu().numpy().view(np.uint64), ec[:, 0])

@@ -184,14 +184,39 @@ def test_spin_32x32_cap26_count_and_ground_state(P):
     state from the tropical backward pass. No oracle reaches this size, so the
     checks are invariants: the configuration attains the returned energy, the
     degeneracy is even (spin-flip symmetry), every tensor fits the cap, and the
-    CRT of the first three residues already gives the whole count (so the five
-    residues agree on one integer below the three-prime range)."""
+    CRT of the first three planes' residues already gives the whole count (so the
+    five planes agree on one integer below the three-plane range)."""
     inst = synth.square_lattice(32, seed=synth.config_seed(3, 0))
     res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=26, n_primes=5).solve(inst, count=True, config=True)
     assert res.stats["sc_log2"] <= 26
     assert _energy(inst, res.config) == res.energy2
     assert -2 * inst.m <= res.energy2 < 0
     assert res.count > 0 and res.count % 2 == 0
-    assert P.crt(res.residues[:3], res.primes[:3]) == res.count
+    assert len(res.residues) == 10          # two residues (30-bit primes) per count plane
+    assert P.crt(res.residues[:6], res.primes[:6]) == res.count
     for r, p in zip(res.residues, res.primes):
         assert r == res.count % p
+
+
+@pytest.mark.parametrize("which", ["spin12", "ksg14", "ksg30"])
+def test_wide_counts_give_the_same_answer(P, which):
+    """Count planes of one residue mod 2^61 - c (wide_counts) instead of the default
+    two residues mod 2^30 - d: the same degeneracy, through every kernel family."""
+    if which == "spin12":
+        inst = synth.square_lattice(12, seed=6)
+        opt, cnt = oracle.solve(inst)
+        cap = 9
+    elif which == "ksg14":
+        inst = synth.kings_subgraph(14, 0.8, seed=5, weights="uniform10")
+        opt, cnt = oracle.solve(inst)
+        cap = 12
+    else:
+        with open(GOLDEN) as f:
+            row = json.load(f)["ksg_30x30_f2"][1]
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+        opt, cnt = row["alpha"], int(row["count"])
+        cap = 24
+    for wide in (True, False):
+        res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap, wide_counts=wide).solve(inst, count=True, config=True)
+        _check(inst, res, opt, cnt)
+        assert len(res.residues) == (3 if wide else 6)

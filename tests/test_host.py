@@ -62,6 +62,34 @@ def test_prime_table(P):
             assert not _is_prime(2**61 - c), c
 
 
+def test_prime_pair_table(P):
+    """Pair moduli q1 << 32 | q0: the primes 2^30 - d in ascending d, taken two per
+    modulus, none skipped; above 2^61, so they never read as a 2^61 - c prime."""
+    ms = P.prime_pairs(9)
+    qs = [q for m in ms for q in (m & 0xFFFFFFFF, m >> 32)]
+    ds = [2**30 - q for q in qs]
+    assert ds == sorted(ds) and len(set(ds)) == 18 and ds[-1] < 1024
+    assert all(_is_prime(q) for q in qs)
+    for d in range(1, ds[-1]):
+        if d not in ds:
+            assert not _is_prime(2**30 - d), d
+    assert all(m >= 2**61 for m in ms)
+    assert P._lib.load().bbtn_prime_pairs(10, None) == P._lib.EINVAL
+
+
+@pytest.mark.parametrize("k", [2, 6, 16])
+def test_crt_roundtrip_pair_primes(P, k):
+    """Garner recombination over the unpacked 30-bit primes (what a solve with pair
+    moduli reports)."""
+    qs = [q for m in P.prime_pairs(8) for q in (m & 0xFFFFFFFF, m >> 32)][:k]
+    M = 1
+    for q in qs:
+        M *= q
+    rng = random.Random(k)
+    for x in [0, 1, M - 1] + [rng.randrange(M) for _ in range(20)]:
+        assert P.crt([x % q for q in qs], qs) == x
+
+
 @pytest.mark.parametrize("k", [1, 2, 3, 8])
 def test_crt_roundtrip(P, k):
     ps = P.primes(k)
