@@ -23,7 +23,7 @@ namespace bbtn {
 
 namespace {
 
-constexpr int TM = 64, TN = 64, TK = 16;
+constexpr int TM = 64, TK = 16;   // row tile, summed chunk
 constexpr int kThr = 256;
 
 struct Groups {
@@ -72,24 +72,27 @@ __device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32
 // disjoint from the in-chunk ones and the deposits add)
 __device__ __forceinline__ uint32_t chunk_off(const uint32_t *koff, int k0) { return kof(koff, (uint32_t)k0); }
 
-// load one chunk of values (and counts) into shared memory as [k][m]
-template <int NP, bool PR, int ROWS, int R>
-__device__ __forceinline__ void load_tile(const int32_t *__restrict__ v, const uint64_t *__restrict__ c,
-                                          uint64_t plane, int unit, const Lanes<R> &L, uint32_t kb,
-                                          int32_t *sv, uint64_t *sc) {
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const uint32_t off = L.off[r] + kb;
-        const int32_t x = __ldg(v + off);
-        sv[L.sidx[r]] = x;
-        if constexpr (NP > 0) {
-#pragma unroll
-            for (int t = 0; t < NP; t++)
-                sc[t * TK * (ROWS + 2) + (L.sidx[r] / (ROWS + 4)) * (ROWS + 2) + L.sidx[r] % (ROWS + 4)] =
-                    unit ? (x >= kFiniteMin ? (PR ? 0x100000001ull : 1ull) : 0ull) : __ldg(c + (uint64_t)t * plane + off);
-        }
-    }
+// asynchronous global -> shared copies (no registers held while in flight)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory stage of the counting path: value tiles sA[TK][TM+4], sB[TK][TN+4],
+// then count tiles cA[NP][TK][TM+2], cB[NP][TK][TN+2]; two stages alternate.
+template <int NP, int TN>
+struct CStage {
+    static constexpr size_t kVA = (size_t)TK * (TM + 4) * 4, kVB = (size_t)TK * (TN + 4) * 4;
+    static constexpr size_t kCA = (size_t)NP * TK * (TM + 2) * 8, kCB = (size_t)NP * TK * (TN + 2) * 8;
+    static constexpr size_t kBytes = (kVA + kVB + kCA + kCB + 15) & ~(size_t)15;   // kVA + kVB is a multiple of 16
+};
 
 // 16-bit lanes of the packed value-only path: infeasible entries enter as -2^14, so
 // no sum of two entries leaves the int16 range; a result below -2^13 is infeasible.
@@ -101,8 +104,9 @@ __device__ __forceinline__ uint32_t dup16(int32_t x) { return ((uint32_t)x & 0xf
 template <int NP, bool V16, int TN, bool PR>
 __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups &G, int fastA_k, int fastB_k,
                                            uint64_t tile, unsigned char *smem_raw) {
-    // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], sA[TK][TM+4],
-    // sB[TK][TN+4], counts. TN = 64: 4 x 4 outputs per thread; TN = 16: 4 x 1.
+    // layout: koffA[3][256], koffB[3][256], rowA[TM], colB[TN], rowC[TM], colC[TN], then
+    // sA[TK][TM+4], sB[TK][TN+4] (values only) or two CStage stages (with counts).
+    // TN = 64: 4 x 4 outputs per thread; TN = 16: 4 x 1.
     static_assert(TN == 64 || TN == 16, "column tile");
     static_assert(!V16 || TN == 64, "16-bit lanes pair columns");
     constexpr int MC = TN / 16;              // columns per thread
@@ -117,8 +121,6 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     uint32_t *colC = rowC + TM;
     int32_t(*sA)[TM + 4] = (int32_t(*)[TM + 4])(colC + TN);
     int32_t(*sB)[TN + 4] = (int32_t(*)[TN + 4])((int32_t *)sA + TK * (TM + 4));
-    uint64_t(*cA)[TK][TM + 2] = (uint64_t(*)[TK][TM + 2])(((uintptr_t)((int32_t *)sB + TK * (TN + 4)) + 15) & ~(uintptr_t)15);
-    uint64_t(*cB)[TK][TN + 2] = (uint64_t(*)[TK][TN + 2])((uint64_t *)cA + (NP > 0 ? NP : 1) * TK * (TM + 2));
 
     const int mt = 1 << (G.nm > 6 ? G.nm - 6 : 0);
     const int nt = 1 << (G.nn - TNB);
@@ -261,7 +263,41 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     } else {
         // values and counts in one pass over K. Per chunk: the chunk maximum of each
         // output; a larger one restarts the count, an equal one adds the products of
-        // the chunk's maximising k (summed as 128-bit integers, reduced once).
+        // the chunk's maximising k (summed exactly, reduced once per chunk). The next
+        // chunk's tiles are gathered by asynchronous copies into the other of two
+        // shared-memory stages while the current one is computed. Unit-count operands
+        // copy no counts: a maximising entry is finite, so its count is 1.
+        typedef CStage<NP, TN> St;
+        unsigned char *stage0 = (unsigned char *)(((uintptr_t)(colC + TN) + 15) & ~(uintptr_t)15);
+        const bool ua = P.A.unit_counts, ub = P.B.unit_counts;
+        const uint64_t one = PR ? 0x100000001ull : 1ull;
+        auto issue = [&](int k0, int st) {
+            unsigned char *base = stage0 + st * St::kBytes;
+            int32_t *sv_a = (int32_t *)base, *sv_b = (int32_t *)(base + St::kVA);
+            uint64_t *sc_a = (uint64_t *)(base + St::kVA + St::kVB), *sc_b = (uint64_t *)(base + St::kVA + St::kVB + St::kCA);
+            const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const uint32_t off = LA.off[r] + ka, si = LA.sidx[r];
+                cp_async4(sv_a + si, Av + off);
+                if (!ua) {
+                    const uint32_t ci = (si / (TM + 4)) * (TM + 2) + si % (TM + 4);
+#pragma unroll
+                    for (int t = 0; t < NP; t++) cp_async8(sc_a + t * TK * (TM + 2) + ci, Ac + (uint64_t)t * P.A.plane + off);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RB; r++) {
+                const uint32_t off = LB.off[r] + kb, si = LB.sidx[r];
+                cp_async4(sv_b + si, Bv + off);
+                if (!ub) {
+                    const uint32_t ci = (si / (TN + 4)) * (TN + 2) + si % (TN + 4);
+#pragma unroll
+                    for (int t = 0; t < NP; t++) cp_async8(sc_b + t * TK * (TN + 2) + ci, Bc + (uint64_t)t * P.B.plane + off);
+                }
+            }
+            cp_async_commit();
+        };
         uint64_t acc[4][MC][NP];
 #pragma unroll
         for (int i = 0; i < 4; i++)
@@ -269,10 +305,20 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
             for (int j = 0; j < MC; j++)
 #pragma unroll
                 for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
-        for (int k0 = 0; k0 < K; k0 += TK) {
-            load_tile<NP, PR, TM, 4>(Av, Ac, P.A.plane, P.A.unit_counts, LA, chunk_off(koffA, k0), &sA[0][0], &cA[0][0][0]);
-            load_tile<NP, PR, TN, RB>(Bv, Bc, P.B.plane, P.B.unit_counts, LB, chunk_off(koffB, k0), &sB[0][0], &cB[0][0][0]);
+        issue(0, 0);
+        for (int k0 = 0, st = 0; k0 < K; k0 += TK, st ^= 1) {
+            if (k0 + TK < K) {
+                issue(k0 + TK, st ^ 1);     // that stage was consumed before the last barrier
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
             __syncthreads();
+            unsigned char *base = stage0 + st * St::kBytes;
+            int32_t(*cvA)[TM + 4] = (int32_t(*)[TM + 4])base;
+            int32_t(*cvB)[TN + 4] = (int32_t(*)[TN + 4])(base + St::kVA);
+            uint64_t(*ccA)[TK][TM + 2] = (uint64_t(*)[TK][TM + 2])(base + St::kVA + St::kVB);
+            uint64_t(*ccB)[TK][TN + 2] = (uint64_t(*)[TK][TN + 2])(base + St::kVA + St::kVB + St::kCA);
             int32_t cm[4][MC];
 #pragma unroll
             for (int i = 0; i < 4; i++)
@@ -280,14 +326,14 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                 for (int j = 0; j < MC; j++) cm[i][j] = kNeg;
 #pragma unroll
             for (int kk = 0; kk < TK; kk++) {
-                const int4 a4 = *(const int4 *)&sA[kk][ty * 4];
+                const int4 a4 = *(const int4 *)&cvA[kk][ty * 4];
                 const int a[4] = {a4.x, a4.y, a4.z, a4.w};
                 int bb[MC];
                 if constexpr (MC == 4) {
-                    const int4 b4 = *(const int4 *)&sB[kk][tx * 4];
+                    const int4 b4 = *(const int4 *)&cvB[kk][tx * 4];
                     bb[0] = b4.x; bb[1] = b4.y; bb[2] = b4.z; bb[3] = b4.w;
                 } else {
-                    bb[0] = sB[kk][tx];
+                    bb[0] = cvB[kk][tx];
                 }
 #pragma unroll
                 for (int i = 0; i < 4; i++)
@@ -312,10 +358,10 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                             for (int t = 0; t < NP; t++) s0[t] = s1[t] = 0;
                             for (int kk = 0; kk < TK; kk++) {
-                                if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+                                if (cvA[kk][mi] + cvB[kk][nj] != cm[i][j]) continue;
 #pragma unroll
                                 for (int t = 0; t < NP; t++) {
-                                    const uint64_t x = cA[t][kk][mi], y = cB[t][kk][nj];
+                                    const uint64_t x = ua ? one : ccA[t][kk][mi], y = ub ? one : ccB[t][kk][nj];
                                     s0[t] += (uint64_t)(uint32_t)x * (uint32_t)y;
                                     s1[t] += (uint64_t)(uint32_t)(x >> 32) * (uint32_t)(y >> 32);
                                 }
@@ -332,9 +378,12 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                             for (int t = 0; t < NP; t++) part[t] = 0;
                             for (int kk = 0; kk < TK; kk++) {
-                                if (sA[kk][mi] + sB[kk][nj] != cm[i][j]) continue;
+                                if (cvA[kk][mi] + cvB[kk][nj] != cm[i][j]) continue;
 #pragma unroll
-                                for (int t = 0; t < NP; t++) part[t] += (u128)cA[t][kk][mi] * cB[t][kk][nj];
+                                for (int t = 0; t < NP; t++) {
+                                    const uint64_t x = ua ? one : ccA[t][kk][mi], y = ub ? one : ccB[t][kk][nj];
+                                    part[t] += (u128)x * y;
+                                }
                             }
 #pragma unroll
                             for (int t = 0; t < NP; t++)
@@ -388,9 +437,12 @@ __global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_co
 }
 
 size_t tiled_smem(int np, int tn) {
-    size_t s = 2 * 768 * 4 + 2 * (TM + tn) * 4 + TK * (TM + 4) * 4 + TK * (tn + 4) * 4 + 16;
-    if (np > 0) s += (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (tn + 2) * 8;   // count tiles
-    return s;
+    const size_t head = 2 * 768 * 4 + 2 * (TM + tn) * 4 + 16;
+    const size_t vals = TK * (TM + 4) * 4 + TK * (tn + 4) * 4;
+    if (np == 0) return head + vals;
+    // two stages of value and count tiles (the CStage layout)
+    const size_t stage = (vals + (size_t)np * TK * (TM + 2) * 8 + (size_t)np * TK * (tn + 2) * 8 + 15) & ~(size_t)15;
+    return head + 2 * stage;
 }
 
 // column tile of a step: 64 when its B-only group has at least 6 labels, else 16
