@@ -396,9 +396,15 @@ def run_kernel_case(args):
     gen = torch.Generator(device="cuda").manual_seed(0)
     va = torch.randint(-4, 4, (1 << len(la),), dtype=torch.int32, device="cuda", generator=gen)
     vb = torch.randint(-4, 4, (1 << len(lb),), dtype=torch.int32, device="cuda", generator=gen)
-    ca = torch.randint(0, 1 << 60, (np_, 1 << len(la)), dtype=torch.int64, device="cuda", generator=gen) if np_ else None
-    cb = torch.randint(0, 1 << 60, (np_, 1 << len(lb)), dtype=torch.int64, device="cuda", generator=gen) if np_ else None
-    primes = P.primes(np_)
+    # counts in the solver's form: two residues per word (each below its 30-bit prime)
+    def pair_counts(r):
+        lo = torch.randint(0, 1 << 29, (np_, 1 << r), dtype=torch.int64, device="cuda", generator=gen)
+        hi = torch.randint(0, 1 << 29, (np_, 1 << r), dtype=torch.int64, device="cuda", generator=gen)
+        return lo | (hi << 32)
+
+    ca = pair_counts(len(la)) if np_ else None
+    cb = pair_counts(len(lb)) if np_ else None
+    primes = P.prime_pairs(np_)
     out = (torch.empty(1 << len(lc), dtype=torch.int32, device="cuda"),
            torch.empty((np_, 1 << len(lc)), dtype=torch.int64, device="cuda") if np_ else None)
     def step():

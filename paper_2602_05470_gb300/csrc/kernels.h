@@ -40,9 +40,10 @@ struct ContractParams {
 // the streaming gather kernel (K1 / K3).
 cudaError_t launch_contract(const ContractParams &p, cudaStream_t s, int *kind = nullptr, void *scratch = nullptr,
                             size_t scratch_bytes = 0);   // kind: 0 K1/K3, 2 K1t, 3 K1s
-// K1s: split-K for steps with at most 2^kSplitKMaxOutBits outputs and >= 2^12
-// summed assignments. scratch: device buffer of splitk_scratch_bytes(rc, np).
-constexpr int kSplitKMaxOutBits = 12;
+// K1s: split-K for steps with at most 2^kSplitKMaxOutBits outputs (one grid row per
+// output) and long sums (splitk_eligible). scratch: device buffer of
+// splitk_scratch_bytes(rc, np).
+constexpr int kSplitKMaxOutBits = 15;
 bool splitk_eligible(const ContractParams &p);
 size_t splitk_scratch_bytes(int rc, int np);
 cudaError_t launch_contract_splitk(const ContractParams &p, void *scratch, size_t bytes, cudaStream_t s);

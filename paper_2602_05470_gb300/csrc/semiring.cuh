@@ -95,6 +95,20 @@ __host__ __device__ __forceinline__ uint64_t addmod_pair(uint64_t a, uint64_t b,
 // the count 1 of a plane, and the semiring product / sum of two residue words
 __host__ __device__ __forceinline__ uint64_t count_one(uint32_t c) { return is_pair(c) ? 0x100000001ull : 1ull; }
 
+// the same with the form fixed at compile time (kernels templated on it keep one code path)
+template <bool PR>
+__host__ __device__ __forceinline__ uint64_t rmul(uint64_t a, uint64_t b, uint32_t c) {
+    if constexpr (PR) return mulmod_pair(a, b, c);
+    else return mulmod61(a, b, c);
+}
+template <bool PR>
+__host__ __device__ __forceinline__ uint64_t radd(uint64_t a, uint64_t b, uint32_t c) {
+    if constexpr (PR) return addmod_pair(a, b, c);
+    else return addmod61(a, b, c);
+}
+template <bool PR>
+__host__ __device__ constexpr uint64_t rone() { return PR ? 0x100000001ull : 1ull; }
+
 __host__ __device__ __forceinline__ uint64_t cmul(uint64_t a, uint64_t b, uint32_t c) {
     return is_pair(c) ? mulmod_pair(a, b, c) : mulmod61(a, b, c);
 }

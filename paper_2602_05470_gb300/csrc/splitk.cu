@@ -189,8 +189,12 @@ cudaError_t dispatch(const ContractParams &p, void *scratch, size_t bytes, cudaS
 
 }  // namespace
 
+// Few outputs with long sums: the four-outputs-per-thread kernel would run 2^(rc-2)
+// threads through 2^rs sequential terms each (e.g. 8 threads x 4096 terms for 32
+// outputs), where split-K spreads every output over a block.
 bool splitk_eligible(const ContractParams &p) {
-    return p.rc <= kSplitKMaxOutBits && p.rs >= 12 && p.rs <= 32 && p.np <= 4 && p.rc + p.rs >= 18;
+    if (p.rs > 32 || p.np > 4 || p.rc > kSplitKMaxOutBits) return false;
+    return p.rc <= 12 ? p.rs >= 8 : p.rs >= 9;
 }
 
 size_t splitk_scratch_bytes(int rc, int np) {

@@ -77,7 +77,7 @@ struct Group4 {
     int8_t vecC;       // g = (0, 1) and C is 16-byte aligned: one 128-bit store
 };
 
-template <int NP, bool HASB>
+template <int NP, bool HASB, bool PR>
 __device__ __forceinline__ void contract4_body(const ContractParams &P, const Group4 gr, uint32_t bid,
                                                uint32_t nblk, uint32_t (*tA)[256], uint32_t (*tB)[256],
                                                uint32_t *ktab) {
@@ -181,13 +181,13 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
                             if (P.A.unit_counts) {
                                 term = (HASB && !P.B.unit_counts)
                                            ? __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j])
-                                           : count_one(c);
+                                           : rone<PR>();
                             } else {
                                 const uint64_t x = __ldg(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ej);
                                 if (!HASB || P.B.unit_counts) term = x;
-                                else term = cmul(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
+                                else term = rmul<PR>(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
                             }
-                            acc[j][t] = cadd(acc[j][t], term, c);
+                            acc[j][t] = radd<PR>(acc[j][t], term, c);
                         }
                     }
                 }
@@ -214,13 +214,13 @@ struct S4Args {
     ContractParams p[NB];
 };
 
-template <int NP, bool HASB, int NB>
+template <int NP, bool HASB, int NB, bool PR>
 __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Args<NB> args) {
     __shared__ uint32_t tA[4][256];
     __shared__ uint32_t tB[4][256];
     extern __shared__ uint32_t ktab[];
     if constexpr (NB == 1) {
-        contract4_body<NP, HASB>(args.p[0], args.g[0], blockIdx.x, gridDim.x, tA, tB, ktab);
+        contract4_body<NP, HASB, PR>(args.p[0], args.g[0], blockIdx.x, gridDim.x, tA, tB, ktab);
     } else {
         __shared__ ContractParams sP;
         int e = 0;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Ar
         const uint32_t *src = (const uint32_t *)&args.p[e];
         for (int i = threadIdx.x; i < (int)(sizeof(ContractParams) / 4); i += blockDim.x) ((uint32_t *)&sP)[i] = src[i];
         __syncthreads();
-        contract4_body<NP, HASB>(sP, args.g[e], blockIdx.x - args.blk0[e],
+        contract4_body<NP, HASB, PR>(sP, args.g[e], blockIdx.x - args.blk0[e],
                                  args.blk0[e + 1] - args.blk0[e], tA, tB, ktab);
     }
 }
@@ -251,7 +251,7 @@ Group4 pick_group(const ContractParams &p) {
     return r;
 }
 
-template <int NP, bool HASB, int NB>
+template <int NP, bool HASB, int NB, bool PR>
 cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
     S4Args<NB> a;
     memset(&a, 0, sizeof a);
@@ -273,29 +273,33 @@ cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
     a.blk0[n] = (uint32_t)total;
     const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << ktb);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_contract4<NP, HASB, NB>,
+        cudaError_t e = cudaFuncSetAttribute(k_contract4<NP, HASB, NB, PR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_contract4<NP, HASB, NB><<<(unsigned)total, kThr, smem, s>>>(a);
+    k_contract4<NP, HASB, NB, PR><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <bool HASB, int NB>
 cudaError_t dispatch4(const ContractParams *p, int n, cudaStream_t s) {
+    const bool pr = p[0].np > 0 && is_pair(p[0].cprime[0]);
+#define BBTN_S4_NP(N) \
+    case N: return pr ? launch4<N, HASB, NB, true>(p, n, s) : launch4<N, HASB, NB, false>(p, n, s);
     switch (p[0].np) {
-        case 0: return launch4<0, HASB, NB>(p, n, s);
-        case 1: return launch4<1, HASB, NB>(p, n, s);
-        case 2: return launch4<2, HASB, NB>(p, n, s);
-        case 3: return launch4<3, HASB, NB>(p, n, s);
-        case 4: return launch4<4, HASB, NB>(p, n, s);
-        case 5: return launch4<5, HASB, NB>(p, n, s);
-        case 6: return launch4<6, HASB, NB>(p, n, s);
-        case 7: return launch4<7, HASB, NB>(p, n, s);
-        case 8: return launch4<8, HASB, NB>(p, n, s);
-        case 9: return launch4<9, HASB, NB>(p, n, s);
+        case 0: return launch4<0, HASB, NB, false>(p, n, s);
+        BBTN_S4_NP(1)
+        BBTN_S4_NP(2)
+        BBTN_S4_NP(3)
+        BBTN_S4_NP(4)
+        BBTN_S4_NP(5)
+        BBTN_S4_NP(6)
+        BBTN_S4_NP(7)
+        BBTN_S4_NP(8)
+        BBTN_S4_NP(9)
         default: return cudaErrorInvalidValue;
     }
+#undef BBTN_S4_NP
 }
 
 bool fits4(const ContractParams &p) { return p.rc >= 2 && p.rc <= 30 && p.rs >= 0 && p.rs <= 30; }
@@ -313,7 +317,9 @@ cudaError_t launch_contract_stream4_batch(const ContractParams *p, int n, cudaSt
     if (n <= 0) return cudaSuccess;
     if (n > kBatchMax) return cudaErrorInvalidValue;
     for (int i = 0; i < n; i++)
-        if (!fits4(p[i]) || p[i].np != p[0].np || p[i].hasB != p[0].hasB) return cudaErrorNotSupported;
+        if (!fits4(p[i]) || p[i].np != p[0].np || p[i].hasB != p[0].hasB ||
+            (p[i].np > 0 && is_pair(p[i].cprime[0]) != is_pair(p[0].cprime[0])))
+            return cudaErrorNotSupported;
     if (n == 1) return p[0].hasB ? dispatch4<true, 1>(p, 1, s) : dispatch4<false, 1>(p, 1, s);
     return p[0].hasB ? dispatch4<true, kBatchMax>(p, n, s) : dispatch4<false, kBatchMax>(p, n, s);
 }

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <utility>
 
 #include "kernels.h"
 
@@ -549,45 +550,70 @@ cudaError_t dispatch_split(const ContractParams *p, const Groups *g, const int *
     return cudaSuccess;
 }
 
+// The step with its operands exchanged (max-plus addition commutes): a step with
+// too few A-only labels for a 64-row tile may have enough B-only ones.
+ContractParams swapped(const ContractParams &p) {
+    ContractParams q = p;
+    std::swap(q.A, q.B);
+    for (int i = 0; i < 32; i++) {
+        std::swap(q.oA[i], q.oB[i]);
+        std::swap(q.sA[i], q.sB[i]);
+    }
+    return q;
+}
+
+// make_groups on the step as given, else on its swapped form (q receives the one used)
+bool groups_of(const ContractParams &p, ContractParams &q, Groups &g, int &fa, int &fb) {
+    q = p;
+    if (make_groups(q, g, fa, fb)) return true;
+    if (!p.hasB) return false;
+    q = swapped(p);
+    return make_groups(q, g, fa, fb);
+}
+
 }  // namespace
 
 bool tiled_uses_v16(const ContractParams &p) {
+    ContractParams q;
     Groups g;
     int fa, fb;
-    return p.np == 0 && p.v16 && make_groups(p, g, fa, fb) && column_tile(g) == 64;
+    return p.np == 0 && p.v16 && groups_of(p, q, g, fa, fb) && column_tile(g) == 64;
 }
 
 bool tiled_eligible(const ContractParams &p) {
+    ContractParams q;
     Groups g;
     int fa, fb;
-    return make_groups(p, g, fa, fb);
+    return groups_of(p, q, g, fa, fb);
 }
 
 // Decide whether a step fits the tiled kernel and, if so, launch it.
 // Returns cudaErrorNotSupported when the step has to take the streaming kernel.
 cudaError_t launch_contract_tiled(const ContractParams &p, cudaStream_t s) {
+    ContractParams q;
     Groups g;
     int fa, fb;
-    if (!make_groups(p, g, fa, fb)) return cudaErrorNotSupported;
-    return dispatch_split<1>(&p, &g, &fa, &fb, 1, s);
+    if (!groups_of(p, q, g, fa, fb)) return cudaErrorNotSupported;
+    return dispatch_split<1>(&q, &g, &fa, &fb, 1, s);
 }
 
 cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStream_t s, int lanes) {
     if (n <= 0) return cudaSuccess;
     if (n > kBatchMax || lanes < -1 || lanes > 3) return cudaErrorInvalidValue;
+    ContractParams q[kBatchMax];
     Groups g[kBatchMax];
     int fa[kBatchMax], fb[kBatchMax];
     for (int i = 0; i < n; i++) {
         if (p[i].np != p[0].np || p[i].v16 != p[0].v16 ||
-            (p[i].np > 0 && is_pair(p[i].cprime[0]) != is_pair(p[0].cprime[0])) || !make_groups(p[i], g[i], fa[i], fb[i]))
+            (p[i].np > 0 && is_pair(p[i].cprime[0]) != is_pair(p[0].cprime[0])) || !groups_of(p[i], q[i], g[i], fa[i], fb[i]))
             return cudaErrorNotSupported;
         if (lanes >= 0) {   // the caller's (an autotuner's) choice instead of the bit-0 rule
             fa[i] = lanes & 1;
             fb[i] = (lanes >> 1) & 1;
         }
     }
-    if (n == 1) return dispatch_split<1>(p, g, fa, fb, 1, s);
-    return dispatch_split<kBatchMax>(p, g, fa, fb, n, s);
+    if (n == 1) return dispatch_split<1>(q, g, fa, fb, 1, s);
+    return dispatch_split<kBatchMax>(q, g, fa, fb, n, s);
 }
 
 }  // namespace bbtn

@@ -97,7 +97,7 @@ TILED = [
     (6, 6, 4, 1, "k", "n", "nmb"),
     (7, 6, 6, 2, "k", "k", "bnm"),
     (6, 7, 5, 0, "m", "n", "mn"),
-    (6, 6, 8, 0, "k", "k", "nm"),
+    (6, 6, 8, 2, "k", "k", "nbm"),       # 2^14 outputs, 8 summed: below the split-K range
     (6, 4, 6, 2, "m", "k", "mnb"),       # 4 B-only labels: 64 x 16 tiles
     (7, 5, 8, 1, "k", "n", "bnm"),       # 5 B-only labels
 ]
@@ -263,6 +263,9 @@ def test_backward_selects_a_maximiser(P):
 # assignments); labels: outputs 0-9, summed 100+
 SPLITK = [
     ([0, 1] + list(range(100, 114)), list(range(100, 114)) + [16, 17, 18, 19], [0, 1, 16, 17, 18, 19]),
+    ([0, 1, 2] + list(range(100, 112)), list(range(100, 112)) + [20, 21], [0, 20, 1, 21, 2]),   # 32 outputs x 2^12
+    (list(range(7)) + list(range(100, 109)), list(range(100, 109)) + list(range(10, 17)), list(range(7)) + list(range(10, 17))),  # 2^14 x 2^9
+    ([0, 1, 2, 3] + list(range(100, 108)), list(range(100, 108)) + [4, 5, 6, 7, 8], list(range(9))),   # 2^9 outputs x 2^8
     (list(range(100, 118)), list(range(117, 99, -1)), []),
     ([0, 1, 2] + list(range(100, 116)), None, [2, 0, 1]),
 ]
@@ -287,8 +290,8 @@ def test_contract_splitk_parity(P, case, np_):
 
 
 def test_contract_tiled_long_sum(P):
-    """14 summed labels: beyond a whole-K shared-memory table, still tiled."""
-    la, lb, lc = _tiled_case(6, 6, 14, 0, "k", "k", "mn")
+    """13 summed labels over 2^16 outputs (above the split-K range): tiled."""
+    la, lb, lc = _tiled_case(8, 8, 13, 0, "k", "k", "mn")
     rng = np.random.default_rng(1414)
     primes = P.primes(1)
     A = _rand(rng, len(la), 1, -3, 3, neg_frac=0.02)
@@ -478,3 +481,20 @@ def test_aggregate_pair_moduli(P, n):
     ev, ec = _oracle_pair(list(range(r)), pv, pc, None, None, None, [], moduli)
     assert int(ov_.cpu()[0]) == int(ev[0])
     assert np.array_equal(oc_.cpu().numpy().view(np.uint64), ec[:, 0])
+
+
+@pytest.mark.parametrize("np_", [0, 3])
+def test_contract_tiled_swapped_operands(P, np_):
+    """4 A-only and 12 B-only labels: too few rows for the tile as given, so the
+    operands are exchanged (max-plus addition commutes) and the step is tiled."""
+    M, N, K = [0, 1, 2, 3], list(range(10, 22)), list(range(30, 36))
+    la, lb, lc = K + M, N + K, M + N
+    rng = np.random.default_rng(2200 + np_)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), -4, 4, neg_frac=0.05)
+    B = _rand(rng, len(lb), max(np_, 1), -4, 4, neg_frac=0.05)
+    A, B = (A[0], A[1][:np_]), (B[0], B[1][:np_])
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
+    _pair_case(P, la, lb, lc, 2, 2300 + np_, lo=-4, hi=4)
