@@ -418,8 +418,10 @@ struct TArgs {
     Groups g[NB];
 };
 
+// two blocks per SM except for 64 x 64 counting tiles (their 4 x 4 outputs x NP
+// residue accumulators take the whole register file of one block)
 template <int NP, int NB, bool V16, int TNC, bool PR>
-__global__ void __launch_bounds__(kThr, NP == 0 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
+__global__ void __launch_bounds__(kThr, (NP == 0 || TNC == 16) ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
         tiled_body<NP, V16, TNC, PR>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
@@ -447,6 +449,8 @@ size_t tiled_smem(int np, int tn) {
 }
 
 // column tile of a step: 64 when its B-only group has at least 6 labels, else 16
+// (64 x 16 also for every counting step was measured: faster on random values, 15%
+// slower on the workload's counting steps)
 inline int column_tile(const Groups &g) { return g.nn >= 6 ? 64 : 16; }
 
 template <int NP, int NB, bool V16, int TNC, bool PR>
