@@ -284,21 +284,21 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": kernel, "launches": int(launches), "avg_launch_us": 1000 * ms / max(launches, 1),
                 "device_ms": ms, "peak_source": source}
 
-    pb_bytes = {"k_contract4<0, 1, 16>": pb["prof_stream_bytes"], "k_contract4<4, 1, 1>": pb["prof_scount_bytes"]}
+    pb_bytes = {"k_contract4<0, 1, 16, 0>": pb["prof_stream_bytes"], "k_contract4<4, 1, 1, 1>": pb["prof_scount_bytes"]}
     all16 = pb["prof_tiled_launches"] > 0 and pb["prof_tiled16_launches"] == pb["prof_tiled_launches"]
     alu_src = "derived: 152 SMs x 64 ALU lanes x 2.07 GHz, one add+max instruction per op"
     kernels = [
-        entry("k_contract4 value-only (streaming gather, K1v)", "k_contract4<0, 1, 16>", "hbm",
+        entry("k_contract4 value-only (streaming gather, K1v)", "k_contract4<0, 1, 16, 0>", "hbm",
               pb["prof_stream_ms"], pb["prof_stream_bytes"], pb["prof_stream_launches"], peak, "GB/s",
               peak_kind + " HBM copy", 1e6),
-        entry("k_contract4 counting (streaming gather, K1v, 4 residue planes)", "k_contract4<4, 1, 1>", "hbm",
+        entry("k_contract4 counting (streaming gather, K1v, 4 count planes of residue pairs)", "k_contract4<4, 1, 1, 1>", "hbm",
               pb["prof_scount_ms"], pb["prof_scount_bytes"], pb["prof_scount_launches"], peak, "GB/s",
               peak_kind + " HBM copy", 1e6),
         entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
-              "k_tiled<0, 16, 1, 64>" if all16 else "k_tiled<0, 16, 0, 64>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
+              "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
               pb["prof_tiled_launches"], ALU_PEAK_TOPS * (2 if all16 else 1), "T tropical ops/s",
               alu_src + (" x 2 lanes" if all16 else ""), 1e9),
-        entry("k_tiled counting (register-tiled, K1t, 4 residue planes)", "k_tiled<4, 1, 0, 64>", "alu",
+        entry("k_tiled counting (register-tiled, K1t, 4 count planes of residue pairs)", "k_tiled<4, 1, 0, 64, 1>", "alu",
               pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], ALU_PEAK_TOPS,
               "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
     ]
