@@ -6,7 +6,9 @@
  *
  * The library contracts tropical tensor networks over the counting max-plus
  * semiring. Every tensor element is an int32 value plus an exact degeneracy count
- * carried as residues modulo up to BBTN_MAX_PRIMES primes p_t = 2^61 - c_t.
+ * carried in up to BBTN_MAX_PRIMES count planes of uint64 words: one residue per
+ * word modulo a prime 2^61 - c (bbtn_primes), or two residues per word modulo a
+ * pair of primes 2^30 - d (bbtn_prime_pairs; the solver's default).
  *
  * Conventions shared by every call
  *  - Return value: BBTN_OK (0) or a negative BBTN_E* code; bbtn_last_error() gives
