@@ -2,11 +2,12 @@
 
 Workload (one "step" = one pass of the whole path over a batch of instances):
 unweighted MIS on random King's subgraphs, 30 x 30 grid, site filling 0.8
-(32 seeded instances; a step solves 8 of them), branch-and-bound contraction with a space cap of 2^24
-elements per tensor, exact degeneracy as residues mod three 61-bit primes (plus
-the overflow-check prime) recombined by CRT. Metric: time-to-exact-count per
-instance (seconds, lower is better), with tropical GOP/s and the HBM roofline
-fraction of the contraction kernels alongside.
+(32 seeded instances; a step solves 8 of them, --streams at a time, each in its
+own context on its own CUDA stream), branch-and-bound contraction with a space cap
+of 2^24 elements per tensor, exact degeneracy in three count planes (two residues
+mod 30-bit primes per word) plus the overflow-check plane, recombined by CRT.
+Metric: time-to-exact-count per instance (seconds, lower is better), with tropical
+GOP/s and the roofline fractions of the contraction kernels alongside.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -187,53 +188,89 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")     # 256 MiB > L2
     per = args.instances_per_step
 
-    def make_solver(profile=False):
+    def make_solver(profile=False, st=None):
         return P.Solver(mode=P.MODE_BBTN, space_cap_log2=CAP, n_primes=3, batch=64, profile=profile,
-                        leaf_trials=args.leaf_trials, stream=stream.cuda_stream)
+                        leaf_trials=args.leaf_trials, stream=(st or stream).cuda_stream)
 
-    solver = make_solver()
-    # host-side helper: finds the next instance's contraction order (into the
-    # library's order cache) on another thread while the current one is solved
-    prep = make_solver()
+    # S solver contexts, each on its own CUDA stream and host thread, take the
+    # step's instances round-robin: one instance's many small launches leave most of
+    # the GPU idle, and another instance's launches fill it
+    S = max(1, args.streams)
+    streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+    solvers = [make_solver(st=streams[w]) for w in range(S)]
+    # host-side helpers: find each worker's next instance's contraction order (into
+    # the library's order cache) on another thread while the current one is solved
+    preps = [make_solver(st=streams[w]) for w in range(S)]
 
     per_inst_ms = {}
 
     def one_step(step, timed):
-        st_sum, h2d, d2h = {}, 0, 0
         insts = instances(rank, world, step, per)
         # no order survives from an earlier step: every step finds its own
         P.clear_order_cache()
         t0 = time.perf_counter()
         sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         sa.record(stream)
-        for j, (idx, inst) in enumerate(insts):
-            th = None
-            if not args.no_pipeline and j + 1 < len(insts):
-                th = threading.Thread(target=prep.prepare, args=(insts[j + 1][1],))
+        for w in range(1, S):
+            streams[w].wait_event(sa)
+        parts, errors = [None] * S, []
+
+        def worker(w):
+            try:
+                st_sum, h2d, d2h = {}, 0, 0
+                mine = insts[w::S]
+                for j, (idx, inst) in enumerate(mine):
+                    th = None
+                    if not args.no_pipeline and j + 1 < len(mine):
+                        th = threading.Thread(target=preps[w].prepare, args=(mine[j + 1][1],))
+                        th.start()
+                    solvers[w].load(inst)
+                    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ea.record(streams[w])
+                    res = solvers[w].solve(count=True, config=False)
+                    eb.record(streams[w])
+                    eb.synchronize()
+                    if th is not None:
+                        th.join()
+                    if timed:
+                        per_inst_ms[idx] = ea.elapsed_time(eb)
+                    for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms", "t_plan_s",
+                              "t_device_s", "t_total_s"):
+                        st_sum[k] = st_sum.get(k, 0) + res.stats[k]
+                    h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
+                    d2h += 4 * (res.stats["leaves"] + res.stats["nodes"]) + 4 + 8 * 4   # leaf maxima + result
+                    if timed and step == 0 and args.check:
+                        import json as _j
+                        row = _j.load(open(os.path.join(ROOT, "tests", "golden", "oracle_answers.json")))["ksg_30x30_f2"][idx]
+                        assert res.alpha == row["alpha"] and res.count == int(row["count"]), "mismatch with oracle"
+                parts[w] = (st_sum, h2d, d2h)
+            except BaseException as e:   # re-raised on the main thread
+                errors.append(e)
+
+        if S == 1:
+            worker(0)
+        else:
+            ths = [threading.Thread(target=worker, args=(w,)) for w in range(S)]
+            for th in ths:
                 th.start()
-            solver.load(inst)
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ea.record(stream)
-            res = solver.solve(count=True, config=False)
-            eb.record(stream)
-            eb.synchronize()
-            if th is not None:
+            for th in ths:
                 th.join()
-            if timed:
-                per_inst_ms[idx] = ea.elapsed_time(eb)
-            for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms", "t_plan_s",
-                      "t_device_s", "t_total_s"):
-                st_sum[k] = st_sum.get(k, 0) + res.stats[k]
-            h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
-            d2h += 4 * (res.stats["leaves"] + res.stats["nodes"]) + 4 + 8 * 4   # leaf maxima + result
-            if timed and step == 0 and args.check:
-                import json as _j
-                row = _j.load(open(os.path.join(ROOT, "tests", "golden", "oracle_answers.json")))["ksg_30x30_f2"][idx]
-                assert res.alpha == row["alpha"] and res.count == int(row["count"]), "mismatch with oracle"
+        if errors:
+            raise errors[0]
+        for w in range(1, S):
+            ew = torch.cuda.Event()
+            ew.record(streams[w])
+            stream.wait_event(ew)
         sb.record(stream)
         sb.synchronize()
         dev_ms = sa.elapsed_time(sb)          # the whole step on the device clock
         wall = time.perf_counter() - t0
+        st_sum, h2d, d2h = {}, 0, 0
+        for part in parts:
+            for k, v in part[0].items():
+                st_sum[k] = st_sum.get(k, 0) + v
+            h2d += part[1]
+            d2h += part[2]
         return dev_ms, wall, st_sum, h2d, d2h
 
     for w in range(args.warmup):
@@ -327,7 +364,9 @@ def run_ours(args, rank, world, local_rank):
         k = len(idxs)
         ttn = {"value": t_ttn / k, "unit": "s/instance", "instances": idxs, "slices_log2": slices,
                "bbtn_same_instances": t_bb / k, "bbtn_speedup": t_ttn / t_bb if t_bb else None,
-               "what": "same kernels, dynamic slicing to the same cap, all slices contracted with counts"}
+               "what": "same kernels, dynamic slicing to the same cap, all slices contracted with counts, one "
+                       "instance at a time; bbtn_same_instances is each instance's own span in the timed "
+                       "steps, where --streams instances share the GPU"}
         sl.close()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -339,11 +378,13 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": tot_dev / n_inst, "unit": "s/instance",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot_dev / args.steps, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32+u64(mod 2^61-c)", "data": "synthetic (seeded King's subgraphs)",
+        "vs_baseline": None, "dtype": "int32+u64(two residues mod 2^30-d)", "data": "synthetic (seeded King's subgraphs)",
         "config": {"workload": WORKLOAD, "instances_per_step": per, "instances_total": n_inst,
                    "pipeline": "off" if args.no_pipeline else
                    "the next instance's contraction order is found on a host thread during the current solve",
-                   "timing": "CUDA events on the solver stream around each whole step",
+                   "streams": S,
+                   "timing": "CUDA events around each whole step on the main stream, which the other solver "
+                             "streams join at both ends",
                    "space_cap_log2": CAP, "n_primes": 3, "l2": "256 MiB flush between steps; tensors up to 470 MB"},
         "e2e": {"value": tot_wall / n_inst, "unit": "s/instance",
                 "h2d_bytes_per_step": H2D // args.steps, "d2h_bytes_per_step": D2H // args.steps},
@@ -449,6 +490,8 @@ def main():
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the per-launch roofline pass")
     ap.add_argument("--check", action="store_true", help="compare step 0 with the stored oracle answers")
+    ap.add_argument("--streams", type=int, default=3,
+                    help="solver contexts solving a step's instances concurrently, one CUDA stream and host thread each")
     ap.add_argument("--leaf-trials", type=int, default=0,
                     help="annealing trials for the contraction order of each counting leaf (0: the root order)")
     ap.add_argument("--no-pipeline", action="store_true",

@@ -160,16 +160,16 @@ void DeviceNetwork::set_host(const std::vector<TensorDef> &ts, int nv) {
 }
 
 void DeviceNetwork::upload(cudaStream_t s) {
-    if (vals) cudaFree(vals);
+    if (vals) cudaFreeAsync(vals, s);   // stream-ordered: other streams keep running
     vals = nullptr;
-    BBTN_CUDA(cudaMalloc(&vals, host_vals.size() * sizeof(int32_t)));
+    BBTN_CUDA(cudaMallocAsync(&vals, host_vals.size() * sizeof(int32_t), s));
     BBTN_CUDA(cudaMemcpyAsync(vals, host_vals.data(), host_vals.size() * sizeof(int32_t),
                               cudaMemcpyHostToDevice, s));
     BBTN_CUDA(cudaStreamSynchronize(s));
 }
 
-void DeviceNetwork::release() {
-    if (vals) cudaFree(vals);
+void DeviceNetwork::release(cudaStream_t s) {
+    if (vals) cudaFreeAsync(vals, s);
     vals = nullptr;
 }
 
@@ -520,16 +520,16 @@ static void fill_operand(Operand &o, const Ref &r, const DeviceNetwork &net, cha
 
 void DeviceBuf::reserve(size_t bytes) {
     if (bytes <= size) return;
-    if (ptr) cudaFree(ptr);
+    if (ptr) cudaFreeAsync(ptr, stream);
     ptr = nullptr;
     size = 0;
     const size_t want = std::max(bytes * 2, (size_t)1 << 20);
-    BBTN_CUDA(cudaMalloc(&ptr, want));
+    BBTN_CUDA(cudaMallocAsync(&ptr, want, stream));
     size = want;
 }
 
 DeviceBuf::~DeviceBuf() {
-    if (ptr) cudaFree(ptr);
+    if (ptr) cudaFreeAsync(ptr, stream);
 }
 
 namespace {

@@ -26,7 +26,7 @@ struct DeviceNetwork {
                                              // bounds |value| of every intermediate entry
     void set_host(const std::vector<TensorDef> &ts, int nvars);
     void upload(cudaStream_t s);
-    void release();
+    void release(cudaStream_t s = nullptr);   // stream-ordered free
     ~DeviceNetwork() { release(); }
 };
 
@@ -118,10 +118,13 @@ struct RunStats {
     TileTuner *tuner = nullptr;
 };
 
-// Grow-only device buffer for the fused-subtree programs.
+// Grow-only device buffer for the fused-subtree programs, allocated and freed in
+// the order of `stream` (no device-wide synchronisation, so solves on other
+// streams keep running).
 struct DeviceBuf {
     void *ptr = nullptr;
     size_t size = 0;
+    cudaStream_t stream = nullptr;
     void reserve(size_t bytes);
     ~DeviceBuf();
 };

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThr) k_fused(const __grid_constant__ FusedPar
 template <int NP>
 cudaError_t launch_t(const FusedParams &p, size_t smem, cudaStream_t s) {
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem<k_fused<NP>>();
         if (e != cudaSuccess) return e;
     }
     k_fused<NP><<<(unsigned)p.nsubs, kThr, smem, s>>>(p);

@@ -151,8 +151,7 @@ cudaError_t launch_contract_t(const ContractParams &p, cudaStream_t s) {
     const uint64_t cap = 152ull * 8;
     if (blocks > cap) blocks = cap;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_contract<NP, HASB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem<k_contract<NP, HASB>>();
         if (e != cudaSuccess) return e;
     }
     k_contract<NP, HASB><<<(unsigned)blocks, kThreads, smem, s>>>(p);

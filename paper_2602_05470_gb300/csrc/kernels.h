@@ -7,6 +7,26 @@
 
 namespace bbtn {
 
+// The largest dynamic shared memory a kernel may be launched with is a property of
+// the function (cudaFuncSetAttribute), shared by every host thread of the process.
+// Each kernel that takes more than 48 KB gets it once, at the device's opt-in
+// maximum less its static shared memory, so that launches of different sizes from
+// concurrent host threads (several contexts, one per stream) never race on it.
+template <auto Kernel>
+cudaError_t allow_max_dynamic_smem() {
+    static const cudaError_t e = [] {
+        int dev = 0, optin = 0;
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaGetDevice(&dev);
+        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (r == cudaSuccess) r = cudaFuncGetAttributes(&fa, Kernel);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        return r;
+    }();
+    return e;
+}
+
 // One operand of a pairwise step. Element e of the operand lives at
 // val[base + e] and cnt[t * plane + base + e]; `base` carries the constant
 // offset of variables fixed by slicing / branching (paper Eq. (3): the reduced

@@ -313,8 +313,10 @@ void Solver::ensure_buffers(int64_t n) {
     const int planes = std::max(np_, 1);
     int32_t *nv = nullptr;
     uint64_t *nc = nullptr;
-    BBTN_CUDA(cudaMalloc(&nv, sizeof(int32_t) * (ncap + 1)));
-    BBTN_CUDA(cudaMalloc(&nc, sizeof(uint64_t) * planes * (ncap + 1)));
+    // stream-ordered allocations: no device-wide synchronisation, so solves on
+    // other streams keep running
+    BBTN_CUDA(cudaMallocAsync(&nv, sizeof(int32_t) * (ncap + 1), stream_));
+    BBTN_CUDA(cudaMallocAsync(&nc, sizeof(uint64_t) * planes * (ncap + 1), stream_));
     if (d_val_) {
         BBTN_CUDA(cudaMemcpyAsync(nv, d_val_, sizeof(int32_t), cudaMemcpyDeviceToDevice, stream_));
         for (int t = 0; t < np_; t++)
@@ -327,13 +329,13 @@ void Solver::ensure_buffers(int64_t n) {
     d_cnt_ = nc;
     dcap_ = ncap;
     scratch_bytes_ = aggregate_scratch_bytes(dcap_ + 1, np_) + 256;
-    BBTN_CUDA(cudaMalloc(&d_scratch_, scratch_bytes_));
+    BBTN_CUDA(cudaMallocAsync(&d_scratch_, scratch_bytes_, stream_));
 }
 
 void Solver::release_buffers() {
-    if (d_val_) cudaFree(d_val_);
-    if (d_cnt_) cudaFree(d_cnt_);
-    if (d_scratch_) cudaFree(d_scratch_);
+    if (d_val_) cudaFreeAsync(d_val_, stream_);
+    if (d_cnt_) cudaFreeAsync(d_cnt_, stream_);
+    if (d_scratch_) cudaFreeAsync(d_scratch_, stream_);
     d_val_ = nullptr;
     d_cnt_ = nullptr;
     d_scratch_ = nullptr;
@@ -1146,11 +1148,11 @@ SolveOutput Solver::solve(const Problem &p, bool want_count, bool want_config, b
         finish(want_config);
     } catch (...) {
         release_buffers();
-        net_.release();
+        net_.release(stream_);
         throw;
     }
     release_buffers();
-    net_.release();
+    net_.release(stream_);
     st->t_total_s = now_s() - t0;
     return out_;
 }

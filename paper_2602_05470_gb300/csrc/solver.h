@@ -41,7 +41,9 @@ struct BranchLog {
 class Solver {
   public:
     Solver(const bbtn_opts &o, cudaStream_t s, Arena *arena, TileTuner *tuner = nullptr)
-        : opts_(o), stream_(s), arena_(arena), tuner_(tuner) {}
+        : opts_(o), stream_(s), arena_(arena), tuner_(tuner) {
+        prog_.stream = s;
+    }
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
     // host-only planning summary (bbtn_analyze)
     void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);

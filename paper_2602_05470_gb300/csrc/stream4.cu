@@ -273,8 +273,7 @@ cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
     a.blk0[n] = (uint32_t)total;
     const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << ktb);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_contract4<NP, HASB, NB, PR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem<k_contract4<NP, HASB, NB, PR>>();
         if (e != cudaSuccess) return e;
     }
     k_contract4<NP, HASB, NB, PR><<<(unsigned)total, kThr, smem, s>>>(a);

@@ -471,9 +471,10 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
     }
     a.blk0[n] = (uint32_t)total;
     const size_t smem = tiled_smem(NP, TNC);
-    cudaError_t e = cudaFuncSetAttribute(k_tiled<NP, NB, V16, TNC, PR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > 48 * 1024) {
+        cudaError_t e = allow_max_dynamic_smem<k_tiled<NP, NB, V16, TNC, PR>>();
+        if (e != cudaSuccess) return e;
+    }
     k_tiled<NP, NB, V16, TNC, PR><<<(unsigned)total, kThr, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -220,3 +220,34 @@ def test_wide_counts_give_the_same_answer(P, which):
         res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap, wide_counts=wide).solve(inst, count=True, config=True)
         _check(inst, res, opt, cnt)
         assert len(res.residues) == (3 if wide else 6)
+
+
+def test_concurrent_contexts_on_two_streams(P):
+    """Three contexts, each with its own CUDA stream, solve workload instances at the
+    same time from three host threads (what the benchmark does to fill the GPU):
+    every answer equals the stored oracle answer. Launch-time state shared by the
+    contexts (kernel attributes, the order cache) must not race."""
+    import threading
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"][:6]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    solvers = [P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, stream=st.cuda_stream) for st in streams]
+    out, errors = {}, []
+
+    def work(w):
+        try:
+            for row in rows[w::3]:
+                inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+                r = solvers[w].solve(inst, count=True, config=False)
+                out[row["seed"]] = (r.alpha, r.count)
+        except BaseException as e:
+            errors.append(e)
+
+    ths = [threading.Thread(target=work, args=(w,)) for w in range(3)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert not errors, errors
+    for row in rows:
+        assert out[row["seed"]] == (row["alpha"], int(row["count"]))
