@@ -165,7 +165,12 @@ class Result:
 
 
 class Solver:
-    """Owns one library context (a CUDA stream + device arena)."""
+    """Owns one library context (a CUDA stream + device arena). Keyword options
+    mirror `bbtn_opts` in include/bbtn.h; among them `n_primes` count planes (two
+    residues mod 30-bit primes per word, or one mod a 61-bit prime with
+    `wide_counts=True`) and `leaf_trials` (own contraction orders for counting
+    leaves, off by default). Contexts on different streams may solve concurrently
+    from different host threads."""
 
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
