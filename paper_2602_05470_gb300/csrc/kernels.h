@@ -3,28 +3,37 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "semiring.cuh"
 
 namespace bbtn {
 
 // The largest dynamic shared memory a kernel may be launched with is a property of
-// the function (cudaFuncSetAttribute), shared by every host thread of the process.
-// Each kernel that takes more than 48 KB gets it once, at the device's opt-in
-// maximum less its static shared memory, so that launches of different sizes from
-// concurrent host threads (several contexts, one per stream) never race on it.
+// the function on each device (cudaFuncSetAttribute), shared by every host thread
+// of the process. Each kernel that takes more than 48 KB gets it once per device,
+// at the device's opt-in maximum less its static shared memory, so that launches of
+// different sizes from concurrent host threads (several contexts, one per stream)
+// never race on it.
 template <auto Kernel>
 cudaError_t allow_max_dynamic_smem() {
-    static const cudaError_t e = [] {
-        int dev = 0, optin = 0;
+    constexpr int kMaxDevices = 64;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t err[kMaxDevices];
+    int dev = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r != cudaSuccess) return r;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [dev] {
+        int optin = 0;
         cudaFuncAttributes fa;
-        cudaError_t r = cudaGetDevice(&dev);
-        if (r == cudaSuccess) r = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (r == cudaSuccess) r = cudaFuncGetAttributes(&fa, Kernel);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-        return r;
-    }();
-    return e;
+        cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, Kernel);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        err[dev] = e;
+    });
+    return err[dev];
 }
 
 // One operand of a pairwise step. Element e of the operand lives at
