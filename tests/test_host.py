@@ -237,3 +237,29 @@ def test_prepared_order_is_reused_and_identical(P):
     b = P.Solver(mode=P.MODE_BBTN, space_cap_log2=16).analyze(inst)
     assert a == b
     assert t_cached < t_first
+
+
+@pytest.mark.parametrize("which", ["mixed", "pair_not_prime", "pair_equal", "pair_far", "wide_not_prime"])
+def test_plane_moduli_rejected_before_any_device_work(P, which):
+    """The contraction and both aggregation entry points check every plane modulus
+    (all primes 2^61 - c, or all pairs q1 << 32 | q0 of distinct primes 2^30 - d)
+    before they touch a buffer: bad moduli return BBTN_EINVAL, here without a GPU
+    (the buffer arguments are never dereferenced)."""
+    lib = P._lib.load()
+    wide, pair = P.primes(2), P.prime_pairs(2)
+    q0, q1 = pair[0] & 0xFFFFFFFF, pair[0] >> 32
+    bad = {"mixed": [wide[0], pair[1]],
+           "pair_not_prime": [pair[0], ((q1 - 1) << 32) | q0],      # q1 - 1 is even
+           "pair_equal": [pair[0], (q0 << 32) | q0],
+           "pair_far": [pair[0], (((1 << 30) - 1100) << 32) | q0],   # d >= 1024 is not a pair prime
+           "wide_not_prime": [wide[0], wide[1] - 1]}[which]
+    primes = (C.c_uint64 * 2)(*bad)
+    la = (C.c_int32 * 2)(0, 1)
+    lb = (C.c_int32 * 2)(1, 2)
+    lc = (C.c_int32 * 2)(0, 2)
+    fake = C.c_void_p(1 << 20)    # never dereferenced: validation fails first
+    rc = lib.bbtn_contract(2, la, fake, fake, 2, lb, fake, fake, 2, lc, fake, fake, 2, primes, None)
+    err = lib.bbtn_last_error()
+    assert rc == P._lib.EINVAL and (b"modul" in err or b"prime" in err), err
+    for fn in (lib.bbtn_aggregate, lib.bbtn_aggregate_noalloc):
+        assert fn(4, fake, fake, 2, primes, fake, fake, None) == P._lib.EINVAL
