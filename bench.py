@@ -1,15 +1,27 @@
 """Benchmark: exact ground-state counting with the branch-and-bound tensor network.
 
-Workload (one "step" = one pass of the whole path over a batch of instances):
-unweighted MIS on random King's subgraphs, 30 x 30 grid, site filling 0.8
-(32 seeded instances; a step solves 8 of them, --streams at a time, each in its
+Default workload (one "step" = one pass of the whole path over a batch of
+instances): unweighted MIS on random King's subgraphs, 30 x 30 grid, site filling
+0.8 (32 seeded instances; a step solves 8 of them, --streams at a time, each in its
 own context on its own CUDA stream), branch-and-bound contraction with a space cap
 of 2^24 elements per tensor, exact degeneracy in three count planes (two residues
 mod 30-bit primes per word) plus the overflow-check plane, recombined by CRT.
+Every solved instance is compared with the stored oracle answer after its step,
+outside the timed region.
+
+--workload spin32: the +-J spin glass on the open 32 x 32 square lattice (no
+field, 16 seeded instances), branch-and-bound at a space cap of 2^26, counts as
+residues mod three 61-bit primes recombined by CRT, and one ground state from the
+tropical backward pass. No oracle reaches 32 x 32, so each instance is checked by
+invariants (the configuration attains the energy, the count is even, every tensor
+fits the cap).
+
 Metric: time-to-exact-count per instance (seconds, lower is better), with tropical
-GOP/s and the roofline fractions of the contraction kernels alongside.
+GOP/s, the roofline fractions of the contraction kernels and plain sliced
+tensor-network contraction on the same GPU alongside.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ksg30|spin32] [--kernel-case NAME]
 """
 from __future__ import annotations
 
@@ -19,30 +31,50 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_GRID, FILLING, CAP, N_INST = 30, 0.8, 24, 32
-# integer-ALU peak for the tiled kernel (one add+max instruction per tropical
-# multiply-add): 152 SMs x 64 ALU lanes per SM per clock x 2.07 GHz
-ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
-METRIC = "time-to-exact-count per instance (KSG 30x30 MIS, BBTN)"
-WORKLOAD = "mis_kings_subgraph_30x30_filling0.8_cap2^24_bbtn_counting"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_answers.json")
 
 
-def shard_indices(rank: int, world: int, step: int, per_step: int):
+def _ksg30(idx):
+    import synth
+    return synth.kings_subgraph(30, 0.8, seed=synth.config_seed(2, idx))
+
+
+def _spin32(idx):
+    import synth
+    return synth.square_lattice(32, seed=synth.config_seed(3, idx))
+
+
+WORKLOADS = {
+    "ksg30": {
+        "metric": "time-to-exact-count per instance (KSG 30x30 MIS, BBTN)",
+        "name": "mis_kings_subgraph_30x30_filling0.8_cap2^24_bbtn_counting",
+        "gen": _ksg30, "n_inst": 32, "cap": 24, "n_primes": 3, "wide": False, "config": False,
+        "per_step": 8, "streams": 3, "golden": "ksg_30x30_f2",
+        "dtype": "int32+u64(two residues mod 2^30-d)", "data": "synthetic (seeded King's subgraphs)",
+        "l2": "256 MiB flush between steps; tensors up to 470 MB",
+    },
+    "spin32": {
+        "metric": "time-to-exact-count per instance (+-J 32x32 spin glass, BBTN, with one ground state)",
+        "name": "spin_glass_pmJ_32x32_open_nofield_cap2^26_bbtn_counting_3x61bit_primes_ground_state",
+        "gen": _spin32, "n_inst": 16, "cap": 26, "n_primes": 3, "wide": True, "config": True,
+        "per_step": 2, "streams": 2, "golden": None,
+        "dtype": "int32+u64(one residue mod 2^61-c)", "data": "synthetic (seeded +-J lattices)",
+        "l2": "256 MiB flush between steps; tensors up to 2.4 GB",
+    },
+}
+
+
+def shard_indices(rank: int, world: int, step: int, per_step: int, n_inst: int = 32):
     """Workload instances of one rank in one step: the ranks of a step take
     consecutive, disjoint blocks of per_step instances (weak scaling)."""
-    return [(step * per_step * world + rank * per_step + j) % N_INST for j in range(per_step)]
-
-
-def instances(rank: int, world: int, step: int, per_step: int):
-    import synth
-    return [(idx, synth.kings_subgraph(N_GRID, FILLING, seed=synth.config_seed(2, idx)))
-            for idx in shard_indices(rank, world, step, per_step)]
+    return [(step * per_step * world + rank * per_step + j) % n_inst for j in range(per_step)]
 
 
 def max_over_ranks(values, dist, device):
@@ -61,12 +93,15 @@ TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, 
 
 
 def ncu_traffic():
-    """DRAM bytes per launch of each kernel from the committed ncu summary of this
-    workload (its table rows read '| `kernel` (...) | launches | read + write | N MB |')."""
+    """DRAM bytes per launch of each kernel from the committed ncu summary of the
+    30x30 workload (its table rows read '| `kernel` (...) | launches | ... | N MB |').
+    Kernels whose row is marked 'stale' (changed since the capture) are left out."""
     out = {}
     try:
         import re
         for line in open(TRAFFIC_FILE):
+            if "stale" in line:
+                continue
             m = re.match(r"\|\s*`([^`]+)`.*\|\s*([\d.]+)\s*MB\s*\|\s*$", line)
             if m:
                 out[m.group(1)] = float(m.group(2)) * 1e6
@@ -76,16 +111,37 @@ def ncu_traffic():
 
 
 def measured_peaks():
+    """(measured HBM copy GB/s, "measured"), else the recipe's fallback figure."""
+    hbm, src = 6800.0, "fallback"
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             m = json.load(f)
-        return float(m["hbm_gbs"]), "measured"
+        hbm, src = float(m["hbm_gbs"]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        pass
+    return hbm, src
+
+
+ALU_PEAK_FILE = os.path.join(ROOT, "profiles", "alu_peak_gb300.md")
+
+
+def alu_peak():
+    """Integer-ALU peak (T tropical ops/s at one add+max instruction per op, at the
+    maximum SM clock) from the committed microbenchmark record, else the figure
+    derived from 152 SMs x 64 lanes x 2.07 GHz."""
+    try:
+        import re
+        for line in open(ALU_PEAK_FILE):
+            m = re.match(r"\|\s*viaddmax_s32 at max clock\s*\|\s*([\d.]+)\s*\|", line)
+            if m:
+                return float(m.group(1)), "measured (profiles/alu_peak_gb300.md: independent __viaddmax_s32 chains)"
+    except OSError:
+        pass
+    return 152 * 64 * 2.07e9 / 1e12, "derived: 152 SMs x 64 ALU lanes x 2.07 GHz"
 
 
 class Clocks:
-    """nvidia-smi sampler run during the timed region."""
+    """nvidia-smi sampler run during the timed region (samples go to a temp file)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -93,13 +149,12 @@ class Clocks:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.fh = None
         self.gpu = gpu_index
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            self.fh = tempfile.TemporaryFile(mode="w+")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -114,69 +169,108 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                t = [x.strip() for x in line.split(",")]
-                if len(t) < 9:
-                    continue
-                try:
-                    sm.append(float(t[1]))
-                    smax = float(t[2])
-                except ValueError:
-                    continue
-                for nm, v in zip(names, t[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+        self.fh.seek(0)
+        for line in self.fh:
+            t = [x.strip() for x in line.split(",")]
+            if len(t) < 9:
+                continue
+            try:
+                sm.append(float(t[1]))
+                smax = float(t[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, t[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        self.fh.close()
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_time(per: int, start: int = 0):
-    """Time the CPU oracle (King's-subgraph transfer matrix, one host core) on
-    `per` instances of the workload; returns (seconds per instance, description)."""
+def oracle_time(wl, per: int, start: int = 0):
+    """The CPU oracle on the host cores (one core) on a bounded sample of the
+    workload: (seconds per instance, description, estimate flag). The 30x30 King's
+    subgraphs are solved whole by the sparse transfer matrix. The 32 x 32 lattice
+    is beyond the oracle (2^32 frontier states with big-integer counts), so the
+    lattice transfer matrix is timed on 20 x 20 lattices and scaled by its cost
+    L^2 2^L to L = 32: an estimate, labelled as such."""
     import oracle
     import synth
     oracle.build()
-    t = 0.0
-    idxs = []
+    t, idxs = 0.0, []
     for j in range(per):
-        idx = (start + j) % N_INST
-        inst = synth.kings_subgraph(N_GRID, FILLING, seed=synth.config_seed(2, idx))
-        t0 = time.perf_counter()
-        oracle.mwis_ksg_tm(inst)
+        idx = (start + j) % wl["n_inst"]
+        if wl is WORKLOADS["spin32"]:
+            inst = synth.square_lattice(20, seed=synth.config_seed(3, idx))
+            t0 = time.perf_counter()
+            oracle.spin_square_tm(inst)
+        else:
+            inst = wl["gen"](idx)
+            t0 = time.perf_counter()
+            oracle.solve(inst)
         t += time.perf_counter() - t0
         idxs.append(idx)
-    return t / per, f"instances {idxs} of the 32 (full 30x30 instances, exact count)"
+    if wl is WORKLOADS["spin32"]:
+        scale = (32 * 32 * 2.0 ** 32) / (20 * 20 * 2.0 ** 20)
+        return (t / per) * scale, (f"20x20 +-J lattices (seeds of instances {idxs}), lattice transfer-matrix oracle, "
+                                   f"one core, {t / per:.2f} s each, scaled by L^2 2^L to 32x32 (x{scale:.0f})"), True
+    return t / per, f"instances {idxs} of the {wl['n_inst']} (whole instances, exact count)", False
 
 
-def run_reference(args, rank, world):
+def run_reference(args, rank, world, wl):
     """--impl reference: the oracle as it stands, on the host cores, rank 0 only."""
     if rank != 0:
         return
     for w in range(args.warmup):
-        oracle_time(1, start=w)
-    samples = []
+        oracle_time(wl, 1, start=w)
+    samples, desc, est = [], "", False
     for s in range(args.steps):
-        v, _ = oracle_time(1, start=args.warmup + s)
+        v, desc, est = oracle_time(wl, 1, start=args.warmup + s)
         samples.append(v)
     value = sum(samples) / len(samples)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "s/instance",
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": "s/instance",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * value,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded King's subgraphs)",
-        "config": {"workload": WORKLOAD, "instances_per_step": 1, "l2": "inputs are host-side graphs"},
+        "data": wl["data"],
+        "config": {"workload": wl["name"], "instances_per_step": 1, "l2": "inputs are host-side graphs"},
         "cpu_baseline": {"value": value, "unit": "s/instance", "cores": 1, "kind": "oracle",
-                         "sample": "one full 30x30 instance per step, transfer-matrix oracle, single thread"},
+                         "sample": "one instance per step: " + desc, "estimate": est},
         "e2e": {"value": value, "unit": "s/instance", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, world, local_rank):
+def check_answers(wl, answers):
+    """Compare solved instances (idx -> (optimum, count, config, sc_log2)) with the
+    stored oracle answers, or, where no oracle reaches, with invariants. Raises on
+    any mismatch; returns the number of instances checked."""
+    if wl["golden"]:
+        with open(GOLDEN) as f:
+            rows = json.load(f)[wl["golden"]]
+        for idx, (opt, cnt, _, sc) in answers.items():
+            row = rows[idx]
+            if (opt, cnt) != (row["alpha"], int(row["count"])):
+                raise AssertionError(f"instance {idx}: ({opt}, {cnt}) differs from the oracle's "
+                                     f"({row['alpha']}, {row['count']})")
+            if sc > wl["cap"]:
+                raise AssertionError(f"instance {idx}: a tensor of 2^{sc} elements exceeds the cap")
+        return len(answers)
+    for idx, (e2, cnt, cfg, sc) in answers.items():
+        inst = wl["gen"](idx)
+        e = sum(-2 * J * cfg[i] * cfg[j] for (i, j), J in zip(inst.edges, inst.J))
+        if e != e2:
+            raise AssertionError(f"instance {idx}: the returned configuration has 2H = {e}, not {e2}")
+        if not (-2 * inst.m <= e2 < 0) or cnt <= 0 or cnt % 2:
+            raise AssertionError(f"instance {idx}: E2 = {e2}, D = {cnt} violate the invariants")
+        if sc > wl["cap"]:
+            raise AssertionError(f"instance {idx}: a tensor of 2^{sc} elements exceeds the cap")
+    return len(answers)
+
+
+def run_ours(args, rank, world, local_rank, wl):
     import torch
     import paper_2602_05470_gb300 as P
     dist = None
@@ -186,26 +280,30 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")     # 256 MiB > L2
-    per = args.instances_per_step
+    per = args.instances_per_step or wl["per_step"]
+    cap, spin = wl["cap"], wl["golden"] is None
 
-    def make_solver(profile=False, st=None):
-        return P.Solver(mode=P.MODE_BBTN, space_cap_log2=CAP, n_primes=3, batch=64, profile=profile,
-                        leaf_trials=args.leaf_trials, stream=(st or stream).cuda_stream)
+    def make_solver(profile=False, st=None, mode=None, **kw):
+        return P.Solver(mode=P.MODE_BBTN if mode is None else mode, space_cap_log2=cap, n_primes=wl["n_primes"],
+                        wide_counts=wl["wide"], batch=64, profile=profile, leaf_trials=args.leaf_trials,
+                        stream=(st or stream).cuda_stream, **kw)
+
+    def step_instances(step):
+        return [(idx, wl["gen"](idx)) for idx in shard_indices(rank, world, step, per, wl["n_inst"])]
 
     # S solver contexts, each on its own CUDA stream and host thread, take the
     # step's instances round-robin: one instance's many small launches leave most of
     # the GPU idle, and another instance's launches fill it
-    S = max(1, args.streams)
+    S = max(1, args.streams or wl["streams"])
     streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
     solvers = [make_solver(st=streams[w]) for w in range(S)]
     # host-side helpers: find each worker's next instance's contraction order (into
     # the library's order cache) on another thread while the current one is solved
     preps = [make_solver(st=streams[w]) for w in range(S)]
-
     per_inst_ms = {}
 
     def one_step(step, timed):
-        insts = instances(rank, world, step, per)
+        insts = step_instances(step)
         # no order survives from an earlier step: every step finds its own
         P.clear_order_cache()
         t0 = time.perf_counter()
@@ -213,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
         sa.record(stream)
         for w in range(1, S):
             streams[w].wait_event(sa)
-        parts, errors = [None] * S, []
+        parts, errors, answers = [None] * S, [], {}
 
         def worker(w):
             try:
@@ -227,22 +325,21 @@ def run_ours(args, rank, world, local_rank):
                     solvers[w].load(inst)
                     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     ea.record(streams[w])
-                    res = solvers[w].solve(count=True, config=False)
+                    res = solvers[w].solve(count=True, config=wl["config"])
                     eb.record(streams[w])
                     eb.synchronize()
                     if th is not None:
                         th.join()
                     if timed:
                         per_inst_ms[idx] = ea.elapsed_time(eb)
+                    answers[idx] = (res.energy2 if spin else res.alpha, res.count, res.config, res.stats["sc_log2"])
                     for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms", "t_plan_s",
                               "t_device_s", "t_total_s"):
                         st_sum[k] = st_sum.get(k, 0) + res.stats[k]
                     h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
                     d2h += 4 * (res.stats["leaves"] + res.stats["nodes"]) + 4 + 8 * 4   # leaf maxima + result
-                    if timed and step == 0 and args.check:
-                        import json as _j
-                        row = _j.load(open(os.path.join(ROOT, "tests", "golden", "oracle_answers.json")))["ksg_30x30_f2"][idx]
-                        assert res.alpha == row["alpha"] and res.count == int(row["count"]), "mismatch with oracle"
+                    if wl["config"]:
+                        d2h += inst.n
                 parts[w] = (st_sum, h2d, d2h)
             except BaseException as e:   # re-raised on the main thread
                 errors.append(e)
@@ -271,12 +368,12 @@ def run_ours(args, rank, world, local_rank):
                 st_sum[k] = st_sum.get(k, 0) + v
             h2d += part[1]
             d2h += part[2]
-        return dev_ms, wall, st_sum, h2d, d2h
+        return dev_ms, wall, st_sum, h2d, d2h, answers
 
     for w in range(args.warmup):
         one_step(w + 1000, False)
     clocks = Clocks(local_rank) if not args.no_clocks else None
-    tot_dev, tot_wall, stats, H2D, D2H = 0.0, 0.0, {}, 0, 0
+    tot_dev, tot_wall, stats, H2D, D2H, checked, timed_idx = 0.0, 0.0, {}, 0, 0, 0, []
     if clocks:
         clocks.start()
     for s in range(args.steps):
@@ -284,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        dev_ms, wall, st, h2d, d2h = one_step(s, True)
+        dev_ms, wall, st, h2d, d2h, answers = one_step(s, True)
         torch.cuda.synchronize()
         tot_dev += dev_ms / 1000.0
         tot_wall += wall
@@ -292,112 +389,147 @@ def run_ours(args, rank, world, local_rank):
         D2H += d2h
         for k, v in st.items():
             stats[k] = stats.get(k, 0) + v
+        timed_idx += sorted(answers)
+        if not args.no_check:                             # outside the timed bracket
+            checked += check_answers(wl, answers)
     ck = clocks.stop() if clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
     tot_dev, tot_wall = max_over_ranks([tot_dev, tot_wall], dist, "cuda")
     n_inst = per * args.steps * world
-    # roofline: one more pass over the timed instances with every contraction launch
-    # bracketed by CUDA events on this stream (not part of the timed region)
+    distinct = sorted(set(timed_idx))
+    # roofline: one more pass over the distinct timed instances with every contraction
+    # launch bracketed by CUDA events on the solver's stream (not part of the timed region)
     keys = ("prof_ms", "prof_bytes", "prof_ops", "prof_launches", "prof_stream_ms", "prof_stream_bytes",
             "prof_stream_launches", "prof_scount_ms", "prof_scount_bytes", "prof_scount_launches",
             "prof_tiled_ms", "prof_tiled_ops", "prof_tiled_launches", "prof_tiled16_launches", "prof_tcount_ms",
             "prof_tcount_ops", "prof_tcount_launches")
     pb = {k: 0.0 for k in keys}
+    prof_idx = distinct[:args.profile_instances if args.profile_instances >= 0 else (2 if spin else 32)]
     if not args.no_profile_pass:
         prof = make_solver(profile=True)
-        for s in range(args.steps):
+        for idx in prof_idx:
             P.clear_order_cache()
-            for _, inst in instances(rank, world, s, per):
-                r = prof.solve(inst, count=True, config=False)
-                for k in pb:
-                    pb[k] += r.stats[k]
+            r = prof.solve(wl["gen"](idx), count=True, config=False)
+            for k in pb:
+                pb[k] += r.stats[k]
+        prof.close()
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic()
+    alu, alu_src = alu_peak()
+    traffic = ncu_traffic() if not spin else {}
 
-    def entry(kernel, ncu_name, bound, ms, work, launches, pk, unit, source, scale):
+    def entry(kernel, ncu_name, bound, ms, work, launches, pk, unit, source, scale, bytes_=None):
         ach = work / (ms * scale) if ms else 0.0
         return {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
                 "traffic": traffic.get(ncu_name), "traffic_source": TRAFFIC_SOURCE if ncu_name in traffic else None,
-                "algorithmic_bytes_per_launch": (pb_bytes.get(ncu_name, 0.0) / max(launches, 1)) or None,
+                "algorithmic_bytes_per_launch": (bytes_ / max(launches, 1)) if bytes_ else None,
                 "kernel": kernel, "launches": int(launches), "avg_launch_us": 1000 * ms / max(launches, 1),
                 "device_ms": ms, "peak_source": source}
 
-    pb_bytes = {"k_contract4<0, 1, 16, 0>": pb["prof_stream_bytes"], "k_contract4<4, 1, 1, 1>": pb["prof_scount_bytes"]}
     all16 = pb["prof_tiled_launches"] > 0 and pb["prof_tiled16_launches"] == pb["prof_tiled_launches"]
-    alu_src = "derived: 152 SMs x 64 ALU lanes x 2.07 GHz, one add+max instruction per op"
+    planes = wl["n_primes"] + 1
+    cform = "residue pairs" if not wl["wide"] else "61-bit residues"
     kernels = [
         entry("k_contract4 value-only (streaming gather, K1v)", "k_contract4<0, 1, 16, 0>", "hbm",
               pb["prof_stream_ms"], pb["prof_stream_bytes"], pb["prof_stream_launches"], peak, "GB/s",
-              peak_kind + " HBM copy", 1e6),
-        entry("k_contract4 counting (streaming gather, K1v, 4 count planes of residue pairs)", "k_contract4<4, 1, 1, 1>", "hbm",
-              pb["prof_scount_ms"], pb["prof_scount_bytes"], pb["prof_scount_launches"], peak, "GB/s",
-              peak_kind + " HBM copy", 1e6),
+              peak_kind + " HBM copy", 1e6, pb["prof_stream_bytes"]),
+        entry(f"k_contract4 counting (streaming gather, K1v, {planes} count planes of {cform})",
+              "k_contract4<4, 1, 1, 1>", "hbm", pb["prof_scount_ms"], pb["prof_scount_bytes"],
+              pb["prof_scount_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6, pb["prof_scount_bytes"]),
         entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
-              "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", "alu", pb["prof_tiled_ms"], pb["prof_tiled_ops"],
-              pb["prof_tiled_launches"], ALU_PEAK_TOPS * (2 if all16 else 1), "T tropical ops/s",
+              "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", "alu", pb["prof_tiled_ms"],
+              pb["prof_tiled_ops"], pb["prof_tiled_launches"], alu * (2 if all16 else 1), "T tropical ops/s",
               alu_src + (" x 2 lanes" if all16 else ""), 1e9),
-        entry("k_tiled counting (register-tiled, K1t, 4 count planes of residue pairs)", "k_tiled<4, 1, 0, 64, 1>", "alu",
-              pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], ALU_PEAK_TOPS,
+        entry(f"k_tiled counting (register-tiled, K1t, {planes} count planes of {cform})", "k_tiled<4, 1, 0, 64, 1>",
+              "alu", pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], alu,
               "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
     ]
     order = sorted(range(len(kernels)), key=lambda i: -kernels[i]["device_ms"])
     dominant = dict(kernels[order[0]])
     dominant["share_of_contraction_time"] = dominant["device_ms"] / max(pb["prof_ms"], 1e-9)
+    dominant["profiled_instances"] = prof_idx
     dominant["other_kernels"] = [dict(kernels[i], share_of_contraction_time=kernels[i]["device_ms"] /
                                       max(pb["prof_ms"], 1e-9)) for i in order[1:]]
     # plain tensor-network contraction (dynamic slicing until the cap holds, every
-    # slice contracted, no pruning) on a bounded sample of the timed instances
+    # slice contracted, no pruning) against BBTN, each instance alone on the GPU,
+    # on a sample spread over the timed instances
     ttn = None
-    if rank == 0 and args.ttn_instances > 0:
-        sl = P.Solver(mode=P.MODE_SLICED, space_cap_log2=CAP, n_primes=3, batch=64, stream=stream.cuda_stream)
-        t_ttn, t_bb, idxs, slices = 0.0, 0.0, [], []
-        for idx, inst in instances(rank, world, 0, per)[:args.ttn_instances]:
-            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            sl.load(inst)
-            ea.record(stream)
-            r = sl.solve(count=True, config=False)
-            eb.record(stream)
-            eb.synchronize()
-            t_ttn += ea.elapsed_time(eb) / 1000.0
-            t_bb += per_inst_ms.get(idx, float("nan")) / 1000.0
-            idxs.append(idx)
-            slices.append(r.stats["slices_log2"])
-        k = len(idxs)
-        ttn = {"value": t_ttn / k, "unit": "s/instance", "instances": idxs, "slices_log2": slices,
-               "bbtn_same_instances": t_bb / k, "bbtn_speedup": t_ttn / t_bb if t_bb else None,
-               "what": "same kernels, dynamic slicing to the same cap, all slices contracted with counts, one "
-                       "instance at a time; bbtn_same_instances is each instance's own span in the timed "
-                       "steps, where --streams instances share the GPU"}
+    if rank == 0 and args.ttn_instances != 0:
+        k = args.ttn_instances if args.ttn_instances > 0 else (2 if spin else 8)
+        pick = distinct[::max(1, len(distinct) // k)][:k]
+        sample = 0 if not spin else 16
+        sl = make_solver(mode=P.MODE_SLICED, slice_sample=sample)
+        alone = make_solver()
+        rows = []
+        for idx in pick:
+            inst = wl["gen"](idx)
+            times = []
+            for sv in (sl, alone):
+                P.clear_order_cache()
+                sv.load(inst)
+                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ea.record(stream)
+                r = sv.solve(count=True, config=wl["config"] and sv is alone)
+                eb.record(stream)
+                eb.synchronize()
+                times.append((ea.elapsed_time(eb) / 1000.0, r))
+            (t_sl, r_sl), (t_bb, r_bb) = times
+            full = 2 ** r_sl.stats["slices_log2"]
+            ran = r_sl.stats["slices_run"]
+            if ran == full and (r_sl.energy2 if spin else r_sl.alpha, r_sl.count) != (
+                    r_bb.energy2 if spin else r_bb.alpha, r_bb.count):
+                raise AssertionError(f"instance {idx}: sliced and BBTN answers differ")
+            rows.append({"instance": idx, "slices_log2": r_sl.stats["slices_log2"], "slices_run": ran,
+                         "ttn_s": t_sl * full / ran, "bbtn_alone_s": t_bb,
+                         "speedup": t_sl * full / ran / t_bb})
         sl.close()
+        alone.close()
+        import math
+        ttn = {"unit": "s/instance", "instances": rows,
+               "ttn_mean_s": sum(r["ttn_s"] for r in rows) / len(rows),
+               "bbtn_alone_mean_s": sum(r["bbtn_alone_s"] for r in rows) / len(rows),
+               "speedup_geomean": math.exp(sum(math.log(r["speedup"]) for r in rows) / len(rows)),
+               "estimate": bool(sample),
+               "what": "each instance alone on the GPU, its contraction order found inside the timed call: plain "
+                       "TTN = the same kernels with dynamic slicing to the same cap, every slice contracted with "
+                       "counts, no pruning" + (f" (estimate: the first {sample} slices timed and scaled by "
+                                               "2^slices_log2 / slices_run, the paper's own estimate)" if sample else "")
+                       + "; BBTN alone = the same solve as in the timed steps without other instances sharing the GPU"}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, sample = oracle_time(args.cpu_instances)
-        cpu = {"value": v, "unit": "s/instance", "cores": 1, "kind": "oracle", "sample": sample}
+        v, sample_desc, est = oracle_time(wl, args.cpu_instances)
+        cpu = {"value": v, "unit": "s/instance", "cores": 1, "kind": "oracle", "sample": sample_desc, "estimate": est}
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": tot_dev / n_inst, "unit": "s/instance",
+        "metric": wl["metric"], "value": tot_dev / n_inst, "unit": "s/instance",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot_dev / args.steps, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32+u64(two residues mod 2^30-d)", "data": "synthetic (seeded King's subgraphs)",
-        "config": {"workload": WORKLOAD, "instances_per_step": per, "instances_total": n_inst,
+        "vs_baseline": None, "dtype": wl["dtype"], "data": wl["data"],
+        "config": {"workload": wl["name"], "instances_per_step": per, "instances_total": n_inst,
                    "pipeline": "off" if args.no_pipeline else
                    "the next instance's contraction order is found on a host thread during the current solve",
                    "streams": S,
                    "timing": "CUDA events around each whole step on the main stream, which the other solver "
                              "streams join at both ends",
-                   "space_cap_log2": CAP, "n_primes": 3, "l2": "256 MiB flush between steps; tensors up to 470 MB"},
+                   "space_cap_log2": cap, "n_primes": wl["n_primes"], "l2": wl["l2"]},
+        "checked": (not args.no_check) and checked == len(timed_idx),
+        "checked_instances": checked,
+        "check": ("every timed instance against the stored oracle answer (optimum and exact count), after its "
+                  "step" if wl["golden"] else "every timed instance by invariants (configuration energy, even "
+                  "count, cap), after its step") if not args.no_check else "off",
         "e2e": {"value": tot_wall / n_inst, "unit": "s/instance",
                 "h2d_bytes_per_step": H2D // args.steps, "d2h_bytes_per_step": D2H // args.steps},
         "gpu_launches": int(stats.get("launches", 0)),
         "tropical_gops": stats.get("tropical_ops", 0) / tot_dev / 1e9 if tot_dev else 0.0,
         "leaves_per_instance": stats.get("leaves", 0) / (per * args.steps),
+        "nodes_per_instance": stats.get("nodes", 0) / (per * args.steps),
         # where an instance's time goes (library counters, per instance): host planning
         # (branching, leaf plans and orders), host wall time waiting on leaf windows, and
         # the device time of those windows
         "time_split_ms": {k: 1000 * stats.get(s, 0) / (per * args.steps) for k, s in
                           (("solve_wall", "t_total_s"), ("host_plan", "t_plan_s"), ("device_wait", "t_device_s"))}
         | {"device_windows": stats.get("kernel_ms", 0) / (per * args.steps),
-           "kernels": pb["prof_ms"] / (per * args.steps) if not args.no_profile_pass else None},
+           "kernels": pb["prof_ms"] / max(len(prof_idx), 1) if not args.no_profile_pass else None},
+        "single_instance_s": ttn["bbtn_alone_mean_s"] if ttn else None,
         "leaf_trials": args.leaf_trials,
         "plain_ttn": ttn,
         "roofline": dominant,
@@ -427,16 +559,45 @@ KERNEL_CASES = {
 }
 
 
+def run_alu_peak(args):
+    """Integer-ALU peak: independent dependency chains of the add+max instruction
+    the tiled kernel issues per tropical multiply-add (__viaddmax_s32), and of its
+    two-lane 16-bit form, on 152 x 8 blocks of 256 threads, timed with CUDA events;
+    the SM clock is sampled meanwhile and the rate is also given at the maximum clock."""
+    import torch
+    import paper_2602_05470_gb300 as P
+    torch.cuda.set_device(0)
+    out = {"kernel_case": "alu_peak"}
+    clocks = Clocks(0)
+    for which, name in ((0, "viaddmax_s32"), (1, "viaddmax_s16x2")):
+        P.bench_alu(which, 152 * 8, 256, 4096)                      # warm-up
+        clocks.start()
+        best = None
+        for _ in range(max(args.steps, 3)):
+            ops, ms = P.bench_alu(which, 152 * 8, 256, 1 << 16)
+            rate = ops / ms / 1e9
+            best = rate if best is None else max(best, rate)
+        ck = clocks.stop()
+        at_max = best * ck["sm_max_mhz"] / ck["sm_mhz"] if ck.get("sm_mhz") else None
+        out[name] = {"tops": best, "unit": "T tropical ops/s", "sm_mhz": ck.get("sm_mhz"),
+                     "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons"), "tops_at_max_clock": at_max,
+                     "per_sm_per_clock": (at_max or best) * 1e12 / 152 / ((ck.get("sm_max_mhz") or 2070) * 1e6)}
+    print(json.dumps(out), flush=True)
+
+
 def run_kernel_case(args):
     """One representative contraction step through the C ABI, timed with CUDA events."""
     import torch
     import paper_2602_05470_gb300 as P
+    if args.kernel_case == "alu_peak":
+        return run_alu_peak(args)
     la, lb, lc, np_ = KERNEL_CASES[args.kernel_case]
     v16 = np_ < 0
     np_ = max(np_, 0)
     gen = torch.Generator(device="cuda").manual_seed(0)
     va = torch.randint(-4, 4, (1 << len(la),), dtype=torch.int32, device="cuda", generator=gen)
     vb = torch.randint(-4, 4, (1 << len(lb),), dtype=torch.int32, device="cuda", generator=gen)
+
     # counts in the solver's form: two residues per word (each below its 30-bit prime)
     def pair_counts(r):
         lo = torch.randint(0, 1 << 29, (np_, 1 << r), dtype=torch.int64, device="cuda", generator=gen)
@@ -448,6 +609,7 @@ def run_kernel_case(args):
     primes = P.prime_pairs(np_)
     out = (torch.empty(1 << len(lc), dtype=torch.int32, device="cuda"),
            torch.empty((np_, 1 << len(lc)), dtype=torch.int64, device="cuda") if np_ else None)
+
     def step():
         if v16:
             P.contract_values16(la, va, lb, vb, lc, out=out[0])
@@ -476,22 +638,27 @@ def run_kernel_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES), default=None,
-                    help="time one representative contraction step instead of the workload")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ksg30")
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES) + ["alu_peak"], default=None,
+                    help="time one representative contraction step (or the integer-ALU peak) instead of the workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--instances-per-step", type=int, default=8)
+    ap.add_argument("--instances-per-step", type=int, default=0, help="0: the workload's default")
     ap.add_argument("--cpu-instances", type=int, default=2)
-    ap.add_argument("--ttn-instances", type=int, default=2,
-                    help="timed instances also solved by plain sliced contraction (0: skip)")
+    ap.add_argument("--ttn-instances", type=int, default=-1,
+                    help="timed instances also solved alone by plain sliced contraction and by BBTN "
+                         "(-1: 8 for ksg30, 2 for spin32; 0: skip)")
+    ap.add_argument("--profile-instances", type=int, default=-1,
+                    help="distinct timed instances in the per-launch roofline pass (-1: 32 for ksg30, 2 for spin32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi clock sampler")
     ap.add_argument("--no-profile-pass", action="store_true", help="skip the per-launch roofline pass")
-    ap.add_argument("--check", action="store_true", help="compare step 0 with the stored oracle answers")
-    ap.add_argument("--streams", type=int, default=3,
-                    help="solver contexts solving a step's instances concurrently, one CUDA stream and host thread each")
+    ap.add_argument("--no-check", action="store_true", help="skip the check of every timed instance's answer")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="solver contexts solving a step's instances concurrently, one CUDA stream and host thread "
+                         "each (0: the workload's default, 3 for ksg30, 2 for spin32)")
     ap.add_argument("--leaf-trials", type=int, default=0,
                     help="annealing trials for the contraction order of each counting leaf (0: the root order)")
     ap.add_argument("--no-pipeline", action="store_true",
@@ -501,12 +668,13 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    wl = WORKLOADS[args.workload]
     if args.kernel_case:
         run_kernel_case(args)
     elif args.impl == "reference":
-        run_reference(args, rank, world)
+        run_reference(args, rank, world, wl)
     else:
-        run_ours(args, rank, world, local_rank)
+        run_ours(args, rank, world, local_rank, wl)
 
 
 if __name__ == "__main__":

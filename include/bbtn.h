@@ -87,6 +87,17 @@ int bbtn_prime_pairs(int n, uint64_t *moduli);
 int bbtn_crt_decimal(int k, const uint64_t *res, const uint64_t *primes, char *buf, size_t cap,
                      size_t *needed);
 
+/*
+ * Integer-ALU throughput microbenchmark (measurement only; the paper has no
+ * counterpart): the denominator of the register-tiled kernel's roofline. Runs
+ * blocks x threads threads (threads a multiple of 32, at most 256), each with 8
+ * independent dependency chains of `iters` x 4 add+max instructions: which = 0
+ * __viaddmax_s32 (one tropical multiply-add each), 1 __viaddmax_s16x2 (two).
+ * *ops receives the tropical multiply-adds executed and *ms the kernel's time
+ * (CUDA events on `stream`). Blocking; allocates and frees a small device buffer.
+ */
+int bbtn_bench_alu(int which, int blocks, int threads, int iters, double *ops, float *ms, void *stream);
+
 /* -------------------------------------------------------- device-level operations */
 /*
  * One counting-tropical pairwise contraction (paper Eq. (2), one binary step of
@@ -143,7 +154,10 @@ int bbtn_aggregate(int64_t n, const int32_t *vals, const uint64_t *counts, int n
  * reduction never needs more than that for any n (at most 608 partials of up to
  * 9 planes), and a request that would is rejected with BBTN_EINVAL. The first call
  * on a device looks up the array's device address with that device current, so
- * make that first call before any stream capture. All calls on a device share the
+ * make that first call before any stream capture. The address is looked up once per
+ * device for the life of the process: after cudaDeviceReset on that device it is
+ * stale, so do not call this entry point again on that device in the same process
+ * (bbtn_aggregate has no such limit). All calls on a device share the
  * array and the last call's partials stay in it; nothing in it has to start at
  * zero, but calls that overlap on the GPU (concurrent streams) race on it.
  */
@@ -218,7 +232,15 @@ typedef struct {
                                 matched on the 30x30 King's-subgraph workload) */
     int wide_counts;         /* 1: one residue mod a prime 2^61 - c per count word; 0 (default): two
                                 residues mod primes 2^30 - d per word (bbtn_prime_pairs) */
-    int reserved[2];
+    int slice_sample;        /* sliced mode, timing only: > 0 contracts just the first this-many of
+                                the 2^|V_f| slices (paper, slicing cost estimates: the time of a few
+                                slices times the number of slices); the value and count are then those
+                                of the sampled slices, not of the instance; stats.slices_run counts
+                                them (default 0: every slice) */
+    int arena_budget_mb;     /* device memory the leaf arenas of one launch group may take, in MiB
+                                (default 0: half of the device memory free when the solve starts,
+                                divided among the solves running on the device at that moment); a
+                                single leaf always gets the arena its plan needs */
 } bbtn_opts;
 
 typedef struct {
@@ -258,6 +280,7 @@ typedef struct {
                                 multiply-adds, launches */
     double prof_tcount_ops;
     int64_t prof_tcount_launches;
+    int64_t slices_run;      /* sliced mode: slices contracted (2^slices_log2 unless opts.slice_sample) */
 } bbtn_stats;
 
 /* Fill *opts with defaults. */

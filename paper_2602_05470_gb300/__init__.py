@@ -152,6 +152,15 @@ def contract_backward(la, va, lb, vb, lc, vc, sel_o, stream=None):
     return sa, sb
 
 
+def bench_alu(which: int, blocks: int, threads: int, iters: int, stream=None):
+    """Integer-ALU microbenchmark (0: __viaddmax_s32, 1: __viaddmax_s16x2):
+    (tropical multiply-adds executed, kernel milliseconds)."""
+    lib = _lib.load()
+    ops, ms = C.c_double(), C.c_float()
+    check(lib.bbtn_bench_alu(which, blocks, threads, iters, C.byref(ops), C.byref(ms), _stream(stream)))
+    return ops.value, ms.value
+
+
 @dataclasses.dataclass
 class Result:
     kind: str
@@ -176,7 +185,8 @@ class Solver:
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
                  profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 0, autotune: bool = False,
-                 wide_counts: bool = False, stream=None, workspace=None):
+                 wide_counts: bool = False, slice_sample: int = 0, arena_budget_mb: int = 0, stream=None,
+                 workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
@@ -185,6 +195,7 @@ class Solver:
         o.count_check, o.use_symmetry = count_check, int(use_symmetry)
         o.max_slices_log2, o.profile, o.branch_lookahead = max_slices_log2, int(profile), branch_lookahead
         o.leaf_trials, o.autotune, o.wide_counts = leaf_trials, int(autotune), int(wide_counts)
+        o.slice_sample, o.arena_budget_mb = int(slice_sample), int(arena_budget_mb)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:

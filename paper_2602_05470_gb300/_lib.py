@@ -31,7 +31,7 @@ class Opts(C.Structure):
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
                 ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("leaf_trials", C.c_int),
-                ("autotune", C.c_int), ("wide_counts", C.c_int), ("reserved", C.c_int * 2)]
+                ("autotune", C.c_int), ("wide_counts", C.c_int), ("slice_sample", C.c_int), ("arena_budget_mb", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -46,7 +46,7 @@ class Stats(C.Structure):
                 ("prof_stream_bytes", C.c_double), ("prof_stream_launches", C.c_int64),
                 ("prof_tiled_ms", C.c_double), ("prof_tiled_ops", C.c_double), ("prof_tiled_launches", C.c_int64),
                 ("prof_tiled16_launches", C.c_int64), ("prof_tcount_ms", C.c_double),
-                ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64)]
+                ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64), ("slices_run", C.c_int64)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}
@@ -101,6 +101,7 @@ _SIGS = {
     "bbtn_analyze": ([_vp, _P(PlanInfo), C.c_char_p], C.c_int),
     "bbtn_aggregate_noalloc": ([C.c_int64, _vp, _vp, C.c_int, _u64p, _vp, _vp, _vp], C.c_int),
     "bbtn_aggregate_noalloc_max_scratch": ([], C.c_size_t),
+    "bbtn_bench_alu": ([C.c_int, C.c_int, C.c_int, C.c_int, _P(C.c_double), _f32p, _vp], C.c_int),
     "bbtn_gnn_create": ([C.c_uint64, _P(_vp)], C.c_int),
     "bbtn_gnn_destroy": ([_vp], None),
     "bbtn_gnn_param_count": ([], C.c_int),

@@ -284,6 +284,8 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->leaf_trials = 0;
     o->autotune = 0;
     o->wide_counts = 0;
+    o->slice_sample = 0;
+    o->arena_budget_mb = 0;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -319,7 +321,9 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
 void bbtn_destroy(bbtn_ctx *ctx) {
     if (!ctx) return;
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->arena.stream = ctx->stream;
     ctx->arena.release();
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -327,8 +331,11 @@ void bbtn_destroy(bbtn_ctx *ctx) {
 int bbtn_set_stream(bbtn_ctx *ctx, void *stream) {
     return guarded([&] {
         if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
+        // the arena is freed and regrown in stream order: finish the old stream's use of it first
+        if (ctx->stream) cudaStreamSynchronize(ctx->stream);
         if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
         ctx->stream = (cudaStream_t)stream;
+        ctx->arena.stream = ctx->stream;
         ctx->own_stream = false;
     });
 }

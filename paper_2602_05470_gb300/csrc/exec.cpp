@@ -176,11 +176,11 @@ void DeviceNetwork::release(cudaStream_t s) {
 void Arena::reserve(size_t bytes) {
     if (bytes <= size) return;
     if (!owned) fail(BBTN_ENOMEM, "workspace too small: need " + std::to_string(bytes) + " bytes");
-    if (ptr) cudaFree(ptr);
+    if (ptr) cudaFreeAsync(ptr, stream);   // after the stream's earlier work that used it
     ptr = nullptr;
     size = 0;
     size_t want = std::max(bytes, (size_t)1 << 20);
-    BBTN_CUDA(cudaMalloc(&ptr, want));
+    BBTN_CUDA(cudaMallocAsync(&ptr, want, stream));
     size = want;
 }
 
@@ -192,7 +192,7 @@ void Arena::adopt(void *p, size_t bytes) {
 }
 
 void Arena::release() {
-    if (ptr && owned) cudaFree(ptr);
+    if (ptr && owned) cudaFreeAsync(ptr, stream);
     ptr = nullptr;
     size = 0;
     owned = true;

@@ -150,11 +150,13 @@ void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net,
                      const int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x,
                      cudaStream_t s);
 
-// Grow-only device arena.
+// Grow-only device arena, allocated and freed in the order of `stream` (the owning
+// solver's), so growing it does not wait for other contexts' work on the device.
 struct Arena {
     char *ptr = nullptr;
     size_t size = 0;
     bool owned = true;
+    cudaStream_t stream = nullptr;
     void reserve(size_t bytes);
     void adopt(void *p, size_t bytes);       // caller-owned workspace
     void release();

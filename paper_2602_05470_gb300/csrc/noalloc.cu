@@ -26,7 +26,9 @@ constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of g_noalloc_scratch per device, looked up once with that
-// device current (the host-side symbol is not a device address).
+// device current (the host-side symbol is not a device address). It is kept for
+// the life of the process: a cudaDeviceReset reloads the module, and the entry
+// point's documentation rules out calls after one.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {nullptr};

@@ -451,12 +451,18 @@ void Solver::simplify(std::vector<int8_t> &fx) const {
     }
 }
 
-void Solver::setup(const Problem &p, bool want_count) {
+void Solver::setup(const Problem &p, int active_solves, bool want_count) {
     setup_host(p, want_count);
-    // device memory the leaf arenas of one launch group may take: half of what is free
+    arena_->stream = stream_;
+    // device memory the leaf arenas of one launch group may take: half of what is
+    // free, split among the solves running on this device now (each context's arena
+    // is its own, so concurrent solves must not each plan for the same free memory)
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess)
-        arena_budget_ = (uint64_t)(free_b + (arena_->owned ? arena_->size : 0)) / 2;
+        arena_budget_ = (uint64_t)(free_b + (arena_->owned ? arena_->size : 0)) / 2 /
+                        (uint64_t)std::max(1, active_solves);
+    if (opts_.arena_budget_mb > 0)
+        arena_budget_ = std::min<uint64_t>(arena_budget_, (uint64_t)opts_.arena_budget_mb << 20);
     net_.upload(stream_);
     release_buffers();
     ensure_buffers(std::max(opts_.batch, 1) + 1);
@@ -560,9 +566,11 @@ void Solver::enqueue_leaves(const std::vector<std::vector<int8_t>> &leaves, bool
         st_->sc_log2 = std::max(st_->sc_log2, pl.max_rank);
         st_->steps += (int64_t)pl.steps.size();
     }
-    const uint64_t budget = arena_->owned ? std::max<uint64_t>(arena_budget_, arena_->size) : arena_->size;
+    const uint64_t budget = !arena_->owned ? arena_->size
+                            : opts_.arena_budget_mb > 0 ? arena_budget_
+                                                        : std::max<uint64_t>(arena_budget_, arena_->size);
     const int64_t nb = std::max<int64_t>(1, std::min<int64_t>({(int64_t)kBatchMax, (int64_t)(budget / stride), n}));
-    arena_->reserve(stride * nb);   // growing frees the old arena, which waits for the device
+    arena_->reserve(stride * nb);   // a grown arena replaces the old one in stream order
     for (int64_t i0 = 0; i0 < n; i0 += nb) {
         std::vector<const Plan *> group;
         for (int64_t i = i0; i < std::min(n, i0 + nb); i++) group.push_back(&plans[i]);
@@ -672,7 +680,9 @@ void Solver::run_sliced() {
     const int max_log2 = opts_.max_slices_log2 > 0 ? opts_.max_slices_log2 : 30;
     if ((int)vf.size() > max_log2)
         fail(BBTN_ENOMEM, "slicing needs 2^" + std::to_string(vf.size()) + " slices");
-    const uint64_t ns = 1ull << vf.size();
+    uint64_t ns = 1ull << vf.size();
+    if (opts_.slice_sample > 0) ns = std::min<uint64_t>(ns, (uint64_t)opts_.slice_sample);   // timing only
+    st_->slices_run = (int64_t)ns;
     const int64_t bs = std::max(1, opts_.batch);
     std::vector<std::vector<int8_t>> batch;
     for (uint64_t x = 0; x < ns; x++) {
@@ -1134,12 +1144,45 @@ void Solver::branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st) {
     search(true, log);
 }
 
+namespace {
+
+// Solves in progress per device, so that concurrent contexts split the free device
+// memory between their arenas instead of each planning for all of it.
+struct ActiveSolves {
+    std::mutex mu;
+    std::unordered_map<int, int> n;
+};
+ActiveSolves &active_solves() {
+    static ActiveSolves a;
+    return a;
+}
+struct ActiveSolve {
+    int dev = -1, count = 1;
+    ActiveSolve() {
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            dev = -1;
+        }
+        ActiveSolves &a = active_solves();
+        std::lock_guard<std::mutex> lock(a.mu);
+        count = ++a.n[dev];
+    }
+    ~ActiveSolve() {
+        ActiveSolves &a = active_solves();
+        std::lock_guard<std::mutex> lock(a.mu);
+        --a.n[dev];
+    }
+};
+
+}  // namespace
+
 SolveOutput Solver::solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st) {
     const double t0 = now_s();
     st_ = st;
     memset(st, 0, sizeof(*st));
+    ActiveSolve active;
     try {
-        setup(p, want_count);
+        setup(p, active.count, want_count);
         switch (opts_.mode) {
             case BBTN_MODE_PLAIN: run_plain(); break;
             case BBTN_MODE_SLICED: run_sliced(); break;

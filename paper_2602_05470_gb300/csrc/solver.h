@@ -63,7 +63,7 @@ class Solver {
 
   private:
     struct Leafset;
-    void setup(const Problem &p, bool want_count);
+    void setup(const Problem &p, int active_solves, bool want_count);
     void setup_host(const Problem &p, bool want_count);
     std::vector<int32_t> contract_leaves(const std::vector<std::vector<int8_t>> &leaves, bool counting = true,
                                          const CTree *tree = nullptr);

@@ -122,24 +122,28 @@ def square_lattice(L: int, seed: int = 0, dist: str = "pm1", h2=0, jmax: int = 1
                     geometry={"kind": "square", "L": L, "Lc": Lc})
 
 
-def cubic_lattice(L: int, seed: int = 0, dist: str = "pm1", h2=0) -> Instance:
-    """Open-boundary L x L x L cubic lattice; vertex (x,y,z) -> (x*L + y)*L + z."""
+def cubic_lattice(L: int, seed: int = 0, dist: str = "pm1", h2=0, Ly: Optional[int] = None,
+                  Lz: Optional[int] = None) -> Instance:
+    """Open-boundary L x Ly x Lz cubic lattice (Ly = Lz = L by default); vertex
+    (x, y, z) -> (x * Ly + y) * Lz + z. Edges site by site: +z, +y, +x."""
+    Ly = L if Ly is None else Ly
+    Lz = L if Lz is None else Lz
     rng = SplitMix64(seed)
     edges = []
     for x in range(L):
-        for y in range(L):
-            for z in range(L):
-                v = (x * L + y) * L + z
-                if z + 1 < L:
+        for y in range(Ly):
+            for z in range(Lz):
+                v = (x * Ly + y) * Lz + z
+                if z + 1 < Lz:
                     edges.append((v, v + 1))
-                if y + 1 < L:
-                    edges.append((v, v + L))
+                if y + 1 < Ly:
+                    edges.append((v, v + Lz))
                 if x + 1 < L:
-                    edges.append((v, v + L * L))
+                    edges.append((v, v + Ly * Lz))
     J = _couplings(rng, len(edges), dist, 1)
-    n = L ** 3
+    n = L * Ly * Lz
     h2l = list(h2) if isinstance(h2, (list, tuple)) else [int(h2)] * n
-    return Instance("spin", n, edges, J=J, h2=h2l, geometry={"kind": "cubic", "L": L})
+    return Instance("spin", n, edges, J=J, h2=h2l, geometry={"kind": "cubic", "L": L, "Ly": Ly, "Lz": Lz})
 
 
 def random_regular_graph(n: int, d: int, seed: int = 0, kind: str = "spin",
@@ -190,6 +194,21 @@ def kings_subgraph(N: int, filling: float = 0.8, seed: int = 0, weights: str = "
     Nc = N if Nc is None else Nc
     rng = SplitMix64(seed)
     mask = [1 if rng.uniform() < filling else 0 for _ in range(N * Nc)]
+    inst = kings_mask_graph(N, Nc, mask)
+    if weights == "uniform10":
+        inst.w = [1 + rng.below(10) for _ in range(inst.n)]
+    elif weights != "unit":
+        raise ValueError(weights)
+    return inst
+
+
+def kings_mask_graph(N: int, Nc: int, mask) -> Instance:
+    """Unit-weight King's subgraph of a given row-major 0/1 site mask on an N x Nc
+    grid: kept sites are numbered in row-major order and joined to the kept sites
+    one king move away."""
+    mask = [1 if m else 0 for m in mask]
+    if len(mask) != N * Nc:
+        raise ValueError("mask size")
     vid = [-1] * (N * Nc)
     n = 0
     for s in range(N * Nc):
@@ -207,13 +226,7 @@ def kings_subgraph(N: int, filling: float = 0.8, seed: int = 0, weights: str = "
                 if 0 <= rr < N and 0 <= cc < Nc and mask[rr * Nc + cc]:
                     edges.append((vid[s], vid[rr * Nc + cc]))
     edges.sort()
-    if weights == "unit":
-        w = [1] * n
-    elif weights == "uniform10":
-        w = [1 + rng.below(10) for _ in range(n)]
-    else:
-        raise ValueError(weights)
-    return Instance("mwis", n, edges, w=w,
+    return Instance("mwis", n, edges, w=[1] * n,
                     geometry={"kind": "ksg", "N": N, "Nc": Nc, "mask": mask})
 
 

@@ -251,3 +251,115 @@ def test_concurrent_contexts_on_two_streams(P):
     assert not errors, errors
     for row in rows:
         assert out[row["seed"]] == (row["alpha"], int(row["count"]))
+
+
+def test_ksg_30x30_all_32_instances(P):
+    """Every instance of the 30x30 King's-subgraph workload (filling 0.8, cap 2^24,
+    the benchmark's solver settings) against the stored oracle answers: MIS size,
+    exact degeneracy through the CRT, and an independent set of that size."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"]
+    assert len(rows) == 32
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, n_primes=3, batch=64)
+    for row in rows:
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+        res = s.solve(inst, count=True, config=True)
+        _check(inst, res, row["alpha"], int(row["count"]))
+        assert res.stats["sc_log2"] <= 24
+
+
+def _ksg_rows(rows, pattern):
+    Nc = len(pattern)
+    mask = []
+    for r in range(2 * rows - 1):
+        mask += [int(ch) for ch in pattern] if r % 2 == 0 else [0] * Nc
+    return synth.kings_mask_graph(2 * rows - 1, Nc, mask)
+
+
+@pytest.mark.parametrize("mode", ["plain", "bbtn"])
+def test_multilimb_closed_forms(P, mode):
+    """Degeneracies far beyond 2^64 with closed forms (disjoint unions of small
+    components): on a King's subgraph, 50 rows of a 4-site path (3 maximum sets),
+    a domino (2) and a single site (1): alpha = 200, D = 6^50; on a 14 x 12
+    lattice with zero couplings except 56 isolated J = +1 bonds whose ends carry
+    2h = +2 / -2 (three ground states each) and 56 free spins: E2 = -112,
+    D = 6^56 (about 2^145, inside the three planes' 180-bit CRT range)."""
+    m = P.MODE_PLAIN if mode == "plain" else P.MODE_BBTN
+    cap = 24 if mode == "plain" else 6
+    ksg = _ksg_rows(50, "1111011010")
+    res = P.Solver(mode=m, space_cap_log2=cap, n_primes=3).solve(ksg, count=True, config=True)
+    _check(ksg, res, 200, 6 ** 50)
+    L, Lc = 14, 12
+    inst = synth.square_lattice(L, Lc=Lc, dist="ferro")
+    bonds, h2 = set(), [0] * (L * Lc)
+    for r in range(L):
+        for c in (0, 3, 6, 9):
+            a, b = r * Lc + c, r * Lc + c + 1
+            bonds.add((a, b))
+            h2[a], h2[b] = 2, -2
+    inst.J = [1 if e in bonds else 0 for e in inst.edges]
+    inst.h2 = h2
+    res = P.Solver(mode=m, space_cap_log2=cap, n_primes=3).solve(inst, count=True, config=True)
+    _check(inst, res, -112, 6 ** 56)
+
+
+@pytest.mark.parametrize("shape,seed,h2", [((2, 2, 2), 1, 0), ((3, 3, 2), 2, 0), ((2, 3, 4), 3, 0), ((3, 3, 2), 4, 1)])
+@pytest.mark.parametrize("mode", ["sliced", "bbtn"])
+def test_cubic_lattice_parity(P, shape, seed, h2, mode):
+    """3D open cubic +-J lattices (the paper's other spin-glass topology) small
+    enough for brute force, under slicing and branch-and-bound with a cap below
+    their width."""
+    L, Ly, Lz = shape
+    inst = synth.cubic_lattice(L, seed=seed, Ly=Ly, Lz=Lz, h2=h2)
+    e2, d, _ = oracle.spin_bruteforce(inst)
+    m = P.MODE_SLICED if mode == "sliced" else P.MODE_BBTN
+    res = P.Solver(mode=m, space_cap_log2=3, batch=16).solve(inst, count=True, config=True)
+    _check(inst, res, e2, d)
+    assert res.stats["sc_log2"] <= 3
+
+
+@pytest.mark.parametrize("kind", ["spin", "mwis"])
+@pytest.mark.parametrize("n,seed", [(12, 1), (18, 2), (22, 3)])
+def test_random_regular_parity(P, kind, n, seed):
+    """Random 3-regular graphs (the paper's third topology) small enough for brute
+    force: +-J spin glasses and unweighted MIS, branch-and-bound at cap 2^3."""
+    inst = synth.random_regular_graph(n, 3, seed=seed, kind=kind)
+    if kind == "spin":
+        ref, d, _ = oracle.spin_bruteforce(inst)
+    else:
+        ref, d, _ = oracle.mwis_bruteforce(inst)
+    res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=3, batch=16).solve(inst, count=True, config=True)
+    _check(inst, res, ref, d)
+    assert res.stats["sc_log2"] <= 3
+
+
+def test_concurrent_contexts_with_a_small_arena_budget(P):
+    """Three contexts solve workload instances at once with a 64 MiB cap on the
+    leaf arenas of a launch group (far below one counting leaf's arena): each
+    launch group shrinks to a single leaf and every answer is still the oracle's.
+    Without the cap, concurrent solves split the free device memory among them."""
+    import threading
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"][6:12]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    solvers = [P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, arena_budget_mb=64, stream=st.cuda_stream)
+               for st in streams]
+    out, errors = {}, []
+
+    def work(w):
+        try:
+            for row in rows[w::3]:
+                inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+                r = solvers[w].solve(inst, count=True, config=False)
+                out[row["seed"]] = (r.alpha, r.count)
+        except BaseException as e:
+            errors.append(e)
+
+    ths = [threading.Thread(target=work, args=(w,)) for w in range(3)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    assert not errors, errors
+    for row in rows:
+        assert out[row["seed"]] == (row["alpha"], int(row["count"]))

@@ -62,5 +62,5 @@ def test_two_ranks_shard_the_workload_and_take_the_slowest_time():
             blocks = [gathered[r][s] for r in range(2)]
             flat = [i for blk in blocks for i in blk]
             assert len(flat) == len(set(flat)) == 8          # disjoint, 4 per rank
-            assert sorted(flat) == sorted((s * 8 + j) % b.N_INST for j in range(8))
+            assert sorted(flat) == sorted((s * 8 + j) % b.WORKLOADS["ksg30"]["n_inst"] for j in range(8))
     assert out[0][1] == out[1][1]                          # every rank sees the same plan

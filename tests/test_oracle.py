@@ -329,3 +329,93 @@ def test_contract_network_equals_bruteforce_mwis(seed):
     v, c = _contract_all(_mwis_tn(inst), seed)
     assert v == a
     assert c == [d % p for p in PRIMES]
+
+
+# ---------------------------------------------------------------- multi-limb counts (closed forms)
+#
+# The transfer-matrix oracles add counts as little-endian 64-bit limbs and print
+# them in decimal; every pin above has D < 2^64. These instances are disjoint
+# unions of small components whose optimum and degeneracy are known, so the
+# totals are closed forms that cross 2^64 (one carry into the second limb) and
+# 2^128 (the routine runs out of its two default limbs and is retried with four).
+# A dropped carry, a limb-order slip in the decimal conversion or a lost retry
+# changes the result.
+
+def _ksg_components(rows, pattern):
+    """Mask of `rows` occupied rows (an empty row between consecutive ones, so no
+    king move joins them), each holding the same row pattern."""
+    Nc = len(pattern)
+    N = 2 * rows - 1
+    mask = []
+    for r in range(N):
+        mask += [int(ch) for ch in pattern] if r % 2 == 0 else [0] * Nc
+    return synth.kings_mask_graph(N, Nc, mask)
+
+
+def test_ksg_tm_seventy_dominoes():
+    """70 isolated dominoes (two adjacent sites): each has alpha 1 and 2 maximum
+    sets, so alpha = 70 and D = 2^70 (one carry out of the low limb)."""
+    inst = _ksg_components(35, "11011")
+    assert inst.n == 140 and inst.m == 70
+    assert oracle.mwis_ksg_tm(inst) == (70, 2 ** 70)
+
+
+def test_ksg_tm_paths_dominoes_singles():
+    """Per row: a 4-site path (alpha 2, 3 maximum sets: {1,3}, {1,4}, {2,4}), a
+    domino (1, 2) and a single site (1, 1), separated by empty columns. Over 50
+    rows alpha = 50 * 4 and D = 3^50 * 2^50 = 6^50 > 2^129."""
+    inst = _ksg_components(50, "1111011010")
+    assert inst.n == 50 * 7
+    a, d = oracle.mwis_ksg_tm(inst)
+    assert (a, d) == (200, 6 ** 50)
+    assert d > 2 ** 128
+
+
+def test_ksg_tm_multilimb_with_a_coupled_block():
+    """The same rows plus one full 3x3 king block (alpha 4 with the four corners as
+    the unique maximum set) in an extra row band: alpha and D change by exactly
+    that component's (4, 1)."""
+    base = _ksg_components(40, "1111011010")
+    N, Nc = base.geometry["N"], base.geometry["Nc"]
+    mask = list(base.geometry["mask"]) + [0] * Nc
+    for r in range(3):
+        mask += [1, 1, 1] + [0] * (Nc - 3)
+    inst = synth.kings_mask_graph(N + 4, Nc, mask)
+    assert oracle.mwis_ksg_tm(inst) == (40 * 4 + 4, 6 ** 40)
+
+
+def _square_with(L, Lc, bonds, h2):
+    """L x Lc open lattice with every coupling 0 except `bonds` {(i, j): J}."""
+    inst = synth.square_lattice(L, Lc=Lc, dist="ferro")
+    inst.J = [bonds.get((i, j), 0) for (i, j) in inst.edges]
+    inst.h2 = list(h2)
+    return inst
+
+
+def test_square_tm_free_spins_two_limbs():
+    """9 x 9 lattice with every coupling and field 0: every configuration has
+    energy 0, so D = 2^81."""
+    inst = _square_with(9, 9, {}, [0] * 81)
+    e2, d, _ = oracle.spin_square_tm(inst)
+    assert (e2, d) == (0, 2 ** 81)
+
+
+def test_square_tm_three_state_pairs_four_limbs():
+    """14 x 12 lattice, couplings 0 except the horizontal bonds (c, c+1) for c in
+    {0, 3, 6, 9} of each row, J = +1, with 2h = +2 on the left spin and -2 on the
+    right one. Such a pair has H = -s_a s_b - s_a + s_b: -1 at (+,+), (+,-) and
+    (-,-), +3 at (-,+) -- three ground states. The other spins are free (D = 2
+    each). So E2 = 2 * (-1) * 56 and D = 3^56 * 2^56 = 6^56 > 2^144."""
+    L, Lc = 14, 12
+    bonds, h2 = {}, [0] * (L * Lc)
+    for r in range(L):
+        for c in (0, 3, 6, 9):
+            a, b = r * Lc + c, r * Lc + c + 1
+            bonds[(a, b)] = 1
+            h2[a], h2[b] = 2, -2
+    inst = _square_with(L, Lc, bonds, h2)
+    e2, d, cfg = oracle.spin_square_tm(inst, want_config=True)
+    assert (e2, d) == (-112, 6 ** 56)
+    e = sum(-2 * J * cfg[i] * cfg[j] for (i, j), J in zip(inst.edges, inst.J)) - sum(
+        h * s for h, s in zip(h2, cfg))
+    assert e == e2
