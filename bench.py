@@ -286,7 +286,7 @@ def run_ours(args, rank, world, local_rank, wl):
     def make_solver(profile=False, st=None, mode=None, **kw):
         return P.Solver(mode=P.MODE_BBTN if mode is None else mode, space_cap_log2=cap, n_primes=wl["n_primes"],
                         wide_counts=wl["wide"], batch=64, profile=profile, leaf_trials=args.leaf_trials,
-                        stream=(st or stream).cuda_stream, **kw)
+                        chain_fusion=not args.no_chain_fusion, stream=(st or stream).cuda_stream, **kw)
 
     def step_instances(step):
         return [(idx, wl["gen"](idx)) for idx in shard_indices(rank, world, step, per, wl["n_inst"])]
@@ -334,7 +334,7 @@ def run_ours(args, rank, world, local_rank, wl):
                         per_inst_ms[idx] = ea.elapsed_time(eb)
                     answers[idx] = (res.energy2 if spin else res.alpha, res.count, res.config, res.stats["sc_log2"])
                     for k in ("launches", "tropical_ops", "bytes_moved", "leaves", "nodes", "kernel_ms", "t_plan_s",
-                              "t_device_s", "t_total_s"):
+                              "t_device_s", "t_total_s", "chains", "chained_steps"):
                         st_sum[k] = st_sum.get(k, 0) + res.stats[k]
                     h2d += 16 * len(inst.edges) + 8 * inst.n          # network tensor values uploaded
                     d2h += 4 * (res.stats["leaves"] + res.stats["nodes"]) + 4 + 8 * 4   # leaf maxima + result
@@ -401,7 +401,7 @@ def run_ours(args, rank, world, local_rank, wl):
     keys = ("prof_ms", "prof_bytes", "prof_ops", "prof_launches", "prof_stream_ms", "prof_stream_bytes",
             "prof_stream_launches", "prof_scount_ms", "prof_scount_bytes", "prof_scount_launches",
             "prof_tiled_ms", "prof_tiled_ops", "prof_tiled_launches", "prof_tiled16_launches", "prof_tcount_ms",
-            "prof_tcount_ops", "prof_tcount_launches")
+            "prof_tcount_ops", "prof_tcount_launches", "prof_chain_ms", "prof_chain_bytes", "prof_chain_launches")
     pb = {k: 0.0 for k in keys}
     prof_idx = distinct[:args.profile_instances if args.profile_instances >= 0 else (2 if spin else 32)]
     if not args.no_profile_pass:
@@ -438,6 +438,9 @@ def run_ours(args, rank, world, local_rank, wl):
               "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", "alu", pb["prof_tiled_ms"],
               pb["prof_tiled_ops"], pb["prof_tiled_launches"], alu * (2 if all16 else 1), "T tropical ops/s",
               alu_src + (" x 2 lanes" if all16 else ""), 1e9),
+        entry("k_chain value-only (fused chains of streaming steps, K1m)", "k_chain", "hbm", pb["prof_chain_ms"],
+              pb["prof_chain_bytes"], pb["prof_chain_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6,
+              pb["prof_chain_bytes"]),
         entry(f"k_tiled counting (register-tiled, K1t, {planes} count planes of {cform})", "k_tiled<4, 1, 0, 64, 1>",
               "alu", pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], alu,
               "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
@@ -522,6 +525,9 @@ def run_ours(args, rank, world, local_rank, wl):
         "tropical_gops": stats.get("tropical_ops", 0) / tot_dev / 1e9 if tot_dev else 0.0,
         "leaves_per_instance": stats.get("leaves", 0) / (per * args.steps),
         "nodes_per_instance": stats.get("nodes", 0) / (per * args.steps),
+        "chain_fusion": {"on": not args.no_chain_fusion,
+                         "chains_per_instance": stats.get("chains", 0) / (per * args.steps),
+                         "steps_replaced_per_instance": stats.get("chained_steps", 0) / (per * args.steps)},
         # where an instance's time goes (library counters, per instance): host planning
         # (branching, leaf plans and orders), host wall time waiting on leaf windows, and
         # the device time of those windows
@@ -661,6 +667,8 @@ def main():
                          "each (0: the workload's default, 3 for ksg30, 2 for spin32)")
     ap.add_argument("--leaf-trials", type=int, default=0,
                     help="annealing trials for the contraction order of each counting leaf (0: the root order)")
+    ap.add_argument("--no-chain-fusion", action="store_true",
+                    help="run every value-only step as its own launch (no fused chains; same results)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not find the next instance's contraction order while the current one is solved")
     args = ap.parse_args()

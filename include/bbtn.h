@@ -167,6 +167,27 @@ int bbtn_aggregate_noalloc(int64_t n, const int32_t *vals, const uint64_t *count
 size_t bbtn_aggregate_noalloc_max_scratch(void);
 
 /*
+ * A chain of value-only pairwise steps in one pass (paper Eq. (2) applied L times,
+ * no counts): T_0 = A, T_l = max(BBTN_NEG, max over the labels of T_{l-1} and B_l
+ * missing from lc_l of T_{l-1} + B_l) with labels lc_l, and the result vc = T_L.
+ * Every entry equals what L calls of bbtn_contract (np = 0) give, infeasible
+ * entries included; A is read once and vc written once, and no intermediate is
+ * stored. This is the step pattern in which a big frontier tensor absorbs edge
+ * matrices one after another.
+ * la: host int[ra] labels of A (va: device int32[2^ra]). L: 1..8 steps. rb: host
+ * int[L], ranks 0..4 of the B_l; lb: host labels of B_0..B_{L-1} concatenated; vb:
+ * host array of L device pointers (int32[2^rb[l]] each, never NULL). rc: host
+ * int[L] ranks of the step results; lc: host labels of the results concatenated;
+ * every label of lc_l must be in T_{l-1} or B_l. vc: device int32[2^rc[L-1]], not
+ * aliasing an input. The chain must fit the fused kernel -- at most 3 labels summed
+ * over the whole chain, 2^summed * L <= 16, final rank 2..30 -- else BBTN_EINVAL
+ * (run the steps with bbtn_contract instead). Asynchronous on `stream`.
+ */
+int bbtn_contract_chain(int ra, const int32_t *la, const int32_t *va, int L, const int32_t *rb,
+                        const int32_t *lb, const int32_t *const *vb, const int32_t *rc, const int32_t *lc,
+                        int32_t *vc, void *stream);
+
+/*
  * Value-only variant of bbtn_contract (same step, paper Eq. (2), no counts) for
  * operands whose finite values all lie in (-2^12, 2^12): the register-tiled
  * kernel then adds and maxes two 16-bit lanes per instruction (the solver uses
@@ -241,6 +262,9 @@ typedef struct {
                                 (default 0: half of the device memory free when the solve starts,
                                 divided among the solves running on the device at that moment); a
                                 single leaf always gets the arena its plan needs */
+    int no_chain_fusion;     /* 1: run every value-only step as its own launch instead of fusing
+                                chains of steps in which a big tensor absorbs small network tensors
+                                into one pass (default 0: fused; the results are identical) */
 } bbtn_opts;
 
 typedef struct {
@@ -281,6 +305,11 @@ typedef struct {
     double prof_tcount_ops;
     int64_t prof_tcount_launches;
     int64_t slices_run;      /* sliced mode: slices contracted (2^slices_log2 unless opts.slice_sample) */
+    double prof_chain_ms;    /* fused chains of value-only streaming steps (K1m): device time, */
+    double prof_chain_bytes; /* algorithmic bytes (A read once, the result written once), launches */
+    int64_t prof_chain_launches;
+    int64_t chains;          /* K1m chains launched (one per chain and leaf) */
+    int64_t chained_steps;   /* pairwise steps those chains replaced */
 } bbtn_stats;
 
 /* Fill *opts with defaults. */
@@ -355,7 +384,9 @@ typedef struct {
     double arena_bytes;      /* device arena the static memory plan needs */
     int64_t bb_nodes;        /* BBTN mode: nodes of the search tree, expanded on the host */
     int64_t bb_leaves;       /* BBTN mode: its leaf sub-networks */
-    int reserved[4];
+    int chains;              /* fused chains of value-only steps in the step list (values-only plans) */
+    int chained_steps;       /* the steps they replace */
+    int reserved[2];
 } bbtn_plan_info;
 
 /*
@@ -365,7 +396,10 @@ typedef struct {
  * contracted, so only the heuristic incumbent prunes) and its size reported; with
  * opts.use_gnn and a branch scorer attached, the scorer's forward passes run on
  * the device. If dump_path is not NULL, one CSV line per step is written there:
- * rank_a, rank_b, rank_c, summed, low_identity_bits, bytes, ops.
+ * rank_a, rank_b, rank_c, summed, low_identity_bits, bytes, ops, nb, nm, nn (output bits in both
+ * operands / only A / only B), node, a_node, b_node (tree nodes of the result and the operands),
+ * fused (1 when the step runs inside the fused small-subtree kernel), chain (L on the last step of
+ * a fused chain of L steps, -1 on its earlier steps, 0 elsewhere).
  */
 int bbtn_analyze(bbtn_ctx *ctx, bbtn_plan_info *info, const char *dump_path);
 

@@ -113,6 +113,24 @@ def contract_values16(la, va, lb, vb, lc, out=None, stream=None):
     return vc
 
 
+def contract_chain(la, va, steps, out=None, stream=None):
+    """Value-only chain of steps in one pass: steps = [(lb, vb, lc), ...] (vb a
+    device int32 tensor of 2^len(lb) values, lc the step's output labels); returns
+    the last step's values (device int32[2^len(lc_last)])."""
+    import torch
+    lib = _lib.load()
+    L = len(steps)
+    rb = [len(lb) for lb, _, _ in steps]
+    rc = [len(lc) for _, _, lc in steps]
+    lbs = [x for lb, _, _ in steps for x in lb]
+    lcs = [x for _, _, lc in steps for x in lc]
+    vbs = (C.c_void_p * max(L, 1))(*[vb.data_ptr() for _, vb, _ in steps])
+    vc = torch.empty(1 << rc[-1], dtype=torch.int32, device=va.device) if out is None else out
+    check(lib.bbtn_contract_chain(len(la), i32_array(la), _ptr(va), L, i32_array(rb), i32_array(lbs), vbs,
+                                  i32_array(rc), i32_array(lcs), _ptr(vc), _stream(stream)))
+    return vc
+
+
 def permute(perm, vin, cin, stream=None):
     """out bit q <- in bit perm[q] for the value plane and the count planes."""
     import torch
@@ -185,8 +203,8 @@ class Solver:
                  sa_iters: int = 20, region_size: int = 8, batch: int = 64, use_gnn: bool = False,
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
                  profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 0, autotune: bool = False,
-                 wide_counts: bool = False, slice_sample: int = 0, arena_budget_mb: int = 0, stream=None,
-                 workspace=None):
+                 wide_counts: bool = False, slice_sample: int = 0, arena_budget_mb: int = 0,
+                 chain_fusion: bool = True, stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
@@ -196,6 +214,7 @@ class Solver:
         o.max_slices_log2, o.profile, o.branch_lookahead = max_slices_log2, int(profile), branch_lookahead
         o.leaf_trials, o.autotune, o.wide_counts = leaf_trials, int(autotune), int(wide_counts)
         o.slice_sample, o.arena_budget_mb = int(slice_sample), int(arena_budget_mb)
+        o.no_chain_fusion = int(not chain_fusion)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:

@@ -31,7 +31,7 @@ class Opts(C.Structure):
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
                 ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("leaf_trials", C.c_int),
-                ("autotune", C.c_int), ("wide_counts", C.c_int), ("slice_sample", C.c_int), ("arena_budget_mb", C.c_int)]
+                ("autotune", C.c_int), ("wide_counts", C.c_int), ("slice_sample", C.c_int), ("arena_budget_mb", C.c_int), ("no_chain_fusion", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -46,7 +46,9 @@ class Stats(C.Structure):
                 ("prof_stream_bytes", C.c_double), ("prof_stream_launches", C.c_int64),
                 ("prof_tiled_ms", C.c_double), ("prof_tiled_ops", C.c_double), ("prof_tiled_launches", C.c_int64),
                 ("prof_tiled16_launches", C.c_int64), ("prof_tcount_ms", C.c_double),
-                ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64), ("slices_run", C.c_int64)]
+                ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64), ("slices_run", C.c_int64),
+                ("prof_chain_ms", C.c_double), ("prof_chain_bytes", C.c_double), ("prof_chain_launches", C.c_int64),
+                ("chains", C.c_int64), ("chained_steps", C.c_int64)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}
@@ -56,7 +58,7 @@ class PlanInfo(C.Structure):
     _fields_ = [("tc_log2", C.c_double), ("sc_log2", C.c_int), ("rho", C.c_double),
                 ("slices_log2", C.c_int), ("steps", C.c_int64), ("ops", C.c_double), ("bytes", C.c_double),
                 ("arena_bytes", C.c_double), ("bb_nodes", C.c_int64), ("bb_leaves", C.c_int64),
-                ("reserved", C.c_int * 4)]
+                ("chains", C.c_int), ("chained_steps", C.c_int), ("reserved", C.c_int * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -76,6 +78,8 @@ _SIGS = {
     "bbtn_crt_decimal": ([C.c_int, _u64p, _u64p, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_contract": ([C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp, C.c_int, _i32p, _vp, _vp,
                        C.c_int, _u64p, _vp], C.c_int),
+    "bbtn_contract_chain": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _i32p, _P(_vp), _i32p, _i32p, _vp, _vp],
+                            C.c_int),
     "bbtn_contract_values16": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, _vp], C.c_int),
     "bbtn_permute": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
     "bbtn_search_leaves": ([_vp, C.c_int64, _i8p, _P(C.c_int64)], C.c_int),

@@ -179,6 +179,42 @@ int contract_impl(int ra, const int32_t *la, const int32_t *va, const uint64_t *
 
 }  // namespace
 
+int bbtn_contract_chain(int ra, const int32_t *la, const int32_t *va, int L, const int32_t *rb, const int32_t *lb,
+                        const int32_t *const *vb, const int32_t *rc, const int32_t *lc, int32_t *vc, void *stream) {
+    return guarded([&] {
+        check_labels(ra, la, "A");
+        if (L < 1 || L > kChainMaxSteps || !rb || !rc || !vb || !va || !vc) fail(BBTN_EINVAL, "bad chain arguments");
+        std::vector<int> labA(la, la + ra);
+        std::vector<std::vector<int>> labB(L), labC(L);
+        const int32_t *pb = lb, *pc = lc;
+        std::vector<int> prev = labA;
+        for (int l = 0; l < L; l++) {
+            if (rb[l] < 0 || rb[l] > 4 || !vb[l] || (rb[l] > 0 && !pb))
+                fail(BBTN_EINVAL, "chain: B rank outside 0..4 or B missing");
+            check_labels(rb[l], pb, "B");
+            check_labels(rc[l], pc, "C");
+            labB[l].assign(pb, pb + rb[l]);
+            labC[l].assign(pc, pc + rc[l]);
+            for (int x : labC[l])
+                if (std::find(prev.begin(), prev.end(), x) == prev.end() &&
+                    std::find(labB[l].begin(), labB[l].end(), x) == labB[l].end())
+                    fail(BBTN_EINVAL, "chain: an output label is in neither operand of its step");
+            prev = labC[l];
+            pb += rb[l];
+            pc += rc[l];
+        }
+        ChainParams cp;
+        if (!chain_params(labA, labB, labC, cp))
+            fail(BBTN_EINVAL, "chain does not fit the fused kernel (at most 8 steps, 3 summed labels over the chain, "
+                              "2^summed * steps <= 16, output rank 2..30)");
+        cp.a = va;
+        cp.vc = vc;
+        for (int l = 0; l < L; l++) cp.b[l] = vb[l];
+        cudaError_t e = launch_chain_batch(&cp, 1, (cudaStream_t)stream);
+        if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("chain: ") + cudaGetErrorString(e));
+    });
+}
+
 int bbtn_contract(int ra, const int32_t *la, const int32_t *va, const uint64_t *ca, int rb,
                   const int32_t *lb, const int32_t *vb, const uint64_t *cb, int rc, const int32_t *lc,
                   int32_t *vc, uint64_t *cc, int np, const uint64_t *primes, void *stream) {
@@ -286,6 +322,7 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->wide_counts = 0;
     o->slice_sample = 0;
     o->arena_budget_mb = 0;
+    o->no_chain_fusion = 0;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {

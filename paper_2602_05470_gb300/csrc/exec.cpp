@@ -130,6 +130,7 @@ void Profiler::collect() {
         if (r.kind == 2 || r.kind == 4) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
         if (r.kind == 4) tiled16_launches++;
         if (r.kind == 5) { tcount_ms += t; tcount_ops += r.ops; tcount_launches++; }
+        if (r.kind == 7) { chain_ms += t; chain_bytes += r.bytes; chain_launches++; }
     }
     recs.clear();
     used = 0;
@@ -198,11 +199,131 @@ void Arena::release() {
     owned = true;
 }
 
+// A step that can join a K1m chain: value-only, not fused, its B operand a network
+// tensor of at most 4 physical bits, at most two summed labels, four or more outputs
+// (the register-tiled and split-K kernels never take such a step).
+static bool chain_link(const PStep &ps) {
+    if (ps.fused || !ps.P.hasB || ps.b.kind != 0 || ps.P.np != 0) return false;
+    if (ps.lab_b.size() > 4 || ps.P.rs > 2 || ps.P.rc < 2) return false;
+    return true;
+}
+
+// Kernel parameters of a chain from its labels: A's label at each physical bit
+// (-1 fixed), and for each step the labels of B_l at its physical bits and the
+// labels of the step's result. The chain's output labels are the last step's, its
+// summed labels every label a step sums. False if the chain does not fit the
+// kernel (too many summed labels or steps, a B of more than 4 bits).
+bool chain_params(const std::vector<int> &lab_a, const std::vector<std::vector<int>> &lab_b,
+                  const std::vector<std::vector<int>> &lab_c, ChainParams &cp) {
+    const int L = (int)lab_b.size();
+    if (L < 1 || L > kChainMaxSteps || (int)lab_c.size() != L) return false;
+    const std::vector<int> &out = lab_c[L - 1];
+    const int rc = (int)out.size();
+    if (rc < 2 || rc > 30) return false;
+    std::vector<int> S;
+    for (int k = 0; k < L; k++) {
+        if (lab_b[k].size() > 4) return false;
+        auto in_c = [&](int l) { return std::find(lab_c[k].begin(), lab_c[k].end(), l) != lab_c[k].end(); };
+        for (const auto *labs : {k == 0 ? &lab_a : &lab_c[k - 1], &lab_b[k]})
+            for (int l : *labs)
+                if (l >= 0 && !in_c(l) && std::find(S.begin(), S.end(), l) == S.end()) S.push_back(l);
+    }
+    const int rs = (int)S.size();
+    if (rs > kChainMaxSum || (L << rs) > 16) return false;   // 2^rs * L add+max per output
+    memset(&cp, 0, sizeof cp);
+    cp.rc = rc;
+    cp.rs = rs;
+    cp.L = L;
+    for (int q = 0; q < 32; q++) cp.oA[q] = -1;
+    for (int j = 0; j < kChainMaxSum; j++) cp.sA[j] = -1;
+    auto src = [&](int l) {   // output bit index, 32 + summed index, or -1
+        for (int q = 0; q < rc; q++) if (out[q] == l) return q;
+        for (int j = 0; j < rs; j++) if (S[j] == l) return 32 + j;
+        return -1;
+    };
+    for (size_t q = 0; q < lab_a.size(); q++) {
+        const int l = lab_a[q];
+        if (l < 0) continue;
+        const int w = src(l);
+        if (w < 0) return false;
+        if (w < 32) cp.oA[w] = (int8_t)q;
+        else cp.sA[w - 32] = (int8_t)q;
+    }
+    for (int k = 0; k < L; k++) {
+        for (size_t q = 0; q < lab_b[k].size(); q++) {
+            const int l = lab_b[k][q];
+            if (l < 0) continue;
+            const int w = src(l);
+            if (w < 0) return false;
+            const uint32_t bit = 1u << (4 * k + (int)q);
+            if (w < 32) cp.wC[w] += bit;
+            else cp.wS[w - 32] += bit;
+        }
+        cp.bsize_log2[k] = (int8_t)lab_b[k].size();
+    }
+    return true;
+}
+
+// The chain over steps i0..i1 of a plan (step i + 1 reads step i's result as its A);
+// fills the kernel parameters on step i1.
+static bool build_chain(Plan &plan, int i0, int i1) {
+    const int L = i1 - i0 + 1;
+    if (L < 1 || L > kChainMaxSteps) return false;
+    std::vector<std::vector<int>> lb, lc;
+    for (int i = i0; i <= i1; i++) {
+        const PStep &ps = plan.steps[i];
+        lb.push_back(ps.lab_b);
+        lc.emplace_back(ps.lab_c, ps.lab_c + ps.P.rc);
+    }
+    ChainParams cp;
+    if (!chain_params(plan.steps[i0].lab_a, lb, lc, cp)) return false;
+    PStep &last = plan.steps[i1];
+    for (int k = 0; k < L; k++) last.chain_b[k] = plan.steps[i0 + k].b.off + plan.steps[i0 + k].b.base;
+    last.chain = cp;
+    last.chain_len = L;
+    last.chain_first = i0;
+    for (int i = i0; i < i1; i++) plan.steps[i].chain_len = -1;
+    plan.chains++;
+    plan.chained_steps += L;
+    return true;
+}
+
+// Greedy chains over consecutive linkable steps, each step reading its
+// predecessor's result as A; a run is cut where the next step would break a
+// kernel limit, and only runs of two or more steps are fused.
+static void find_chains(Plan &plan) {
+    const int n = (int)plan.steps.size();
+    int i = 0;
+    while (i < n) {
+        if (!chain_link(plan.steps[i]) || plan.steps[i].a.kind != 1) {
+            i++;
+            continue;
+        }
+        int j = i;
+        std::vector<std::vector<int>> lb{plan.steps[i].lab_b}, lc;
+        lc.emplace_back(plan.steps[i].lab_c, plan.steps[i].lab_c + plan.steps[i].P.rc);
+        while (j + 1 < n && chain_link(plan.steps[j + 1]) && plan.steps[j + 1].a_node == plan.steps[j].node) {
+            // extend only while the longer chain still fits the kernel
+            const PStep &nx = plan.steps[j + 1];
+            lb.push_back(nx.lab_b);
+            lc.emplace_back(nx.lab_c, nx.lab_c + nx.P.rc);
+            ChainParams probe;
+            if (!chain_params(plan.steps[i].lab_a, lb, lc, probe)) break;
+            j++;
+        }
+        if (j > i && build_chain(plan, i, j)) {
+            i = j + 1;
+        } else {
+            i++;
+        }
+    }
+}
+
 // Marks the small subtrees that run fused (every step with at most 2^S outputs and
 // its intermediates fitting in shared memory), lays out their shared memory, and
 // assigns arena blocks in execution order: fused results first, then the other
 // steps in post-order, each block released after its last reader is enqueued.
-static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, FreeList &fl) {
+static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, bool chains, FreeList &fl) {
     const int nsteps = (int)plan.steps.size();
     std::vector<char> fus(t.nodes.size(), 0);
     const int S = np == 0 ? 14 : 11;
@@ -258,6 +379,26 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, Fre
             plan.fused_smem = std::max<size_t>(plan.fused_smem, fsm.peak);
         }
     }
+    for (int i = 0; i < nsteps; i++)
+        if (fus[plan.steps[i].node]) plan.steps[i].fused = true;
+    if (chains && np == 0 && !keep_all) {
+        find_chains(plan);
+        // the fused chain moves A once and C once instead of every intermediate
+        for (int i = 0; i < nsteps; i++) {
+            PStep &ps = plan.steps[i];
+            if (ps.chain_len == 0) continue;
+            plan.bytes -= ps.bytes;
+            if (ps.chain_len > 0) {
+                const PStep &f = plan.steps[ps.chain_first];
+                int ra = 0;
+                for (int l : f.lab_a) ra += l >= 0;
+                ps.bytes = std::ldexp(4.0, ra) + std::ldexp(4.0, ps.P.rc);
+                plan.bytes += ps.bytes;
+            } else {
+                ps.bytes = 0;
+            }
+        }
+    }
     // arena: fused results are alive from the fused launch on
     for (int r : roots)
         if (r != t.root) {
@@ -266,11 +407,22 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, Fre
         }
     for (int i = 0; i < nsteps; i++) {
         PStep &ps = plan.steps[i];
-        if (fus[ps.node]) {
-            ps.fused = true;
+        if (ps.fused) continue;
+        if (ps.chain_len < 0) continue;   // inside a chain: nothing materialised, A stays alive
+        if (ps.c.kind == 1) ps.c.off = fl.alloc(ps.c_block);
+        if (ps.chain_len > 0) {
+            // the chain reads its first step's A (released only now, after C is placed,
+            // so that C never takes A's block) and network tensors
+            const PStep &f = plan.steps[ps.chain_first];
+            ps.chain_a = f.a;
+            const int c = f.a_node;
+            if (c >= 0 && !t.nodes[c].is_leaf()) {
+                const PStep &cs = plan.steps[plan.node_step[c]];
+                ps.chain_a = cs.c;
+                fl.release(cs.c.off, cs.c_block);
+            }
             continue;
         }
-        if (ps.c.kind == 1) ps.c.off = fl.alloc(ps.c_block);
         for (int side = 0; side < 2; side++) {
             const int c = side ? ps.b_node : ps.a_node;
             if (c < 0 || t.nodes[c].is_leaf() || (side == 1 && !ps.P.hasB)) continue;
@@ -344,7 +496,7 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, Fre
 }
 
 Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
-               const uint32_t *cprime, bool keep_all) {
+               const uint32_t *cprime, bool keep_all, bool chains) {
     Plan plan;
     plan.np = np;
     plan.node_step.assign(t.nodes.size(), -1);
@@ -456,9 +608,11 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
             P.sB[j] = B ? (int8_t)B->pos(sum[j]) : -1;
         }
         st.a = A->ref;
+        st.lab_a = A->bit_label;
         P.A.unit_counts = A->unit;
         if (B) {
             st.b = B->ref;
+            st.lab_b = B->bit_label;
             P.B.unit_counts = B->unit;
         }
         View C;
@@ -500,7 +654,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
             view[nd.r].bit_label.clear();
         }
     }
-    finalize_plan(plan, t, np, keep_all, fl);
+    finalize_plan(plan, t, np, keep_all, chains, fl);
     return plan;
 }
 
@@ -679,17 +833,39 @@ void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net,
     for (int i = 1; i < nl; i++)
         if (plans[i]->steps.size() != nsteps) fail(BBTN_ESTATE, "run_plans: plans of different trees");
     std::vector<ContractParams> tiled, strm;
+    std::vector<ChainParams> chain[kChainMaxSteps + 1];
+    double c_bytes[kChainMaxSteps + 1], c_ops[kChainMaxSteps + 1];
     std::vector<double> tb, tops, sb, sops;
     for (size_t k = 0; k < nsteps; k++) {
         tiled.clear();
         strm.clear();
+        for (int l = 0; l <= kChainMaxSteps; l++) {
+            chain[l].clear();
+            c_bytes[l] = c_ops[l] = 0;
+        }
         double t_bytes = 0, t_ops = 0, s_bytes = 0, s_ops = 0;
         for (int i = 0; i < nl; i++) {
             const Plan &pl = *plans[i];
             const PStep &ps = pl.steps[k];
             if (ps.node != plans[0]->steps[k].node) fail(BBTN_ESTATE, "run_plans: plans of different trees");
-            if (ps.fused) continue;
+            if (ps.fused || ps.chain_len < 0) continue;
             char *ar = arena + (uint64_t)i * stride;
+            if (ps.chain_len > 0) {
+                ChainParams cp = ps.chain;
+                Operand a;
+                fill_operand(a, ps.chain_a, net, ar);
+                cp.a = a.val + a.base;
+                cp.vc = ps.c.kind == 2 ? out_val + i : (int32_t *)(ar + ps.c.off);
+                for (int l = 0; l < cp.L; l++) cp.b[l] = net.vals + ps.chain_b[l];
+                chain[cp.L].push_back(cp);
+                c_bytes[cp.L] += ps.bytes;
+                for (int j = ps.chain_first; j <= (int)k; j++) c_ops[cp.L] += pl.steps[j].ops;
+                if (st) {
+                    st->chains++;
+                    st->chained_steps += cp.L;
+                }
+                continue;
+            }
             ContractParams P = ps.P;
             fill_operand(P.A, ps.a, net, ar);
             P.A.unit_counts = ps.a.kind == 0;
@@ -744,6 +920,14 @@ void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net,
             cudaError_t e = launch_contract_stream4_batch(strm.data(), (int)strm.size(), s);
             if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("stream batch: ") + cudaGetErrorString(e));
             lt.done(s_bytes, s_ops, &strm[0], 0, (int)strm.size());
+            if (st) st->launches++;
+        }
+        for (int l = 1; l <= kChainMaxSteps; l++) {
+            if (chain[l].empty()) continue;
+            LaunchTimer lt(pr, s);
+            cudaError_t e = launch_chain_batch(chain[l].data(), (int)chain[l].size(), s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("chain batch: ") + cudaGetErrorString(e));
+            lt.done(c_bytes[l], c_ops[l], nullptr, 7, (int)chain[l].size());
             if (st) st->launches++;
         }
     }

@@ -49,6 +49,15 @@ struct PStep {
     double bytes = 0;      // algorithmic bytes (operands read once, result written once)
     uint64_t c_block = 0;  // arena bytes of the result (kind 1)
     bool fused = false;    // runs inside a fused small-subtree block
+    std::vector<int> lab_a, lab_b;   // label at each physical bit of A / B (-1: fixed bit)
+    // K1m chains (value-only plans): chain_len = L > 0 on the last step of a fused
+    // chain (it writes the chain's result), -1 on the chain's earlier steps (their
+    // results are never materialised)
+    int chain_len = 0;
+    int chain_first = -1;  // the chain's first step (on the last step)
+    ChainParams chain;     // kernel parameters, pointers filled at launch
+    Ref chain_a;           // the chain's A operand
+    uint64_t chain_b[kChainMaxSteps] = {0};   // element offsets of the B operands in the network values
 };
 
 struct Plan {
@@ -67,7 +76,9 @@ struct Plan {
     int64_t fused_steps = 0;
     // scratch of the split-K steps (K1s), at the end of the arena
     uint64_t splitk_off = 0, splitk_bytes = 0;
+    int64_t chains = 0, chained_steps = 0;   // K1m chains and the steps they replace
 };
+
 
 // Element layout of an arena block of rank r with np count planes.
 size_t block_bytes(int r, int np);
@@ -76,8 +87,10 @@ uint64_t count_plane_offset_bytes(int r);
 // Plan the contraction of the network restricted to fx (fx[v] = -1 free, else the
 // fixed value). The result (a scalar) goes to the external destination given at
 // run time. keep_all keeps every intermediate alive (for the backward walk).
+// chains: fuse chains of value-only streaming steps (K1m; plans with np == 0 and
+// without keep_all only).
 Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
-               const uint32_t *cprime, bool keep_all);
+               const uint32_t *cprime, bool keep_all, bool chains = true);
 
 // Per-launch CUDA-event timing of contraction kernels (profile mode): an event
 // pair on the launching stream around each launch, read back after a sync.
@@ -90,7 +103,10 @@ struct Profiler {
     double ms = 0, bytes = 0, ops = 0;
     int64_t launches = 0;
     // per kernel; kind: 0 streaming value-only, 1 fused, 2 tiled value-only (int32),
-    // 3 split-K, 4 tiled value-only (16-bit lanes), 5 tiled counting, 6 streaming counting
+    // 3 split-K, 4 tiled value-only (16-bit lanes), 5 tiled counting, 6 streaming counting,
+    // 7 fused chain (K1m)
+    double chain_ms = 0, chain_bytes = 0;
+    int64_t chain_launches = 0;
     double stream_ms = 0, stream_bytes = 0, scount_ms = 0, scount_bytes = 0;
     double tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0;
     int64_t stream_launches = 0, scount_launches = 0, tiled_launches = 0, tiled16_launches = 0, tcount_launches = 0;
@@ -113,6 +129,7 @@ struct TileTuner {
 
 struct RunStats {
     int64_t launches = 0;
+    int64_t chains = 0, chained_steps = 0;
     double ops = 0, bytes = 0;
     Profiler *prof = nullptr;
     TileTuner *tuner = nullptr;
@@ -128,6 +145,12 @@ struct DeviceBuf {
     void reserve(size_t bytes);
     ~DeviceBuf();
 };
+
+// K1m parameters (pointers excepted) of a chain given by its labels: A's label at
+// each physical bit (-1: fixed), and per step the labels of B_l at its physical
+// bits and of the step's result. False if the chain does not fit the kernel.
+bool chain_params(const std::vector<int> &lab_a, const std::vector<std::vector<int>> &lab_b,
+                  const std::vector<std::vector<int>> &lab_c, ChainParams &cp);
 
 // Enqueue a plan: arena = device base pointer of at least plan.arena_bytes,
 // root result to (out_val[0], out_cnt[t * out_plane]); prog holds the fused

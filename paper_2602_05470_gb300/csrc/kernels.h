@@ -95,6 +95,29 @@ cudaError_t launch_contract_tiled_batch(const ContractParams *p, int n, cudaStre
 bool tiled_eligible(const ContractParams &p);
 bool tiled_uses_v16(const ContractParams &p);   // the value pass runs with two 16-bit lanes
 
+// K1m: a chain of value-only steps in which a big tensor absorbs small network
+// tensors one after another, T_s = max(NEG, max over the labels step s sums of
+// T_{s-1} + B_s), computed in one pass: C[y] = max over every label the chain sums
+// of the left fold acc = max(acc + B_s, NEG) starting from A (max-plus addition
+// distributes over max and both it and the floor are monotone, so this is the
+// step-by-step result exactly, infeasible entries included). A is read once and C
+// written once, where the separate steps read and write every intermediate.
+constexpr int kChainMaxSteps = 8;     // B operands of one chain (4-bit index fields of a 32-bit word)
+constexpr int kChainMaxSum = 3;       // labels summed inside one chain
+struct ChainParams {
+    const int32_t *a = nullptr;       // A value plane, fixed-variable offset applied
+    int32_t *vc = nullptr;
+    int rc = 0, rs = 0, L = 0;
+    int8_t oA[32];                    // A bit of output bit i (-1: not in A)
+    int8_t sA[kChainMaxSum];          // A bit of summed label j (-1: not in A)
+    uint32_t wC[32];                  // output bit i's contribution to the packed B index word
+    uint32_t wS[kChainMaxSum];        // summed label j's contribution (field s: bits 4s..4s+3 index B_s)
+    const int32_t *b[kChainMaxSteps]; // B_s values, fixed-variable offset applied (<= 16 entries)
+    int8_t bsize_log2[kChainMaxSteps];
+};
+// All entries must have the same L (1 <= L <= kChainMaxSteps) and rc >= 2.
+cudaError_t launch_chain_batch(const ChainParams *p, int n, cudaStream_t s);
+
 // out bit q <- in bit perm[q]
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,
                            uint64_t plane_in, int32_t *vout, uint64_t *cout, uint64_t plane_out,

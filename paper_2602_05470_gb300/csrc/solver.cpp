@@ -558,7 +558,9 @@ void Solver::enqueue_leaves(const std::vector<std::vector<int8_t>> &leaves, bool
     // leaf i of a group gets its own arena at i * stride
     const double tp = now_s();
     std::vector<Plan> plans(n);
-    parallel_for(n, [&](int64_t i) { plans[i] = make_plan(tr, net_, leaves[i], counting ? np_ : 0, cprime_, false); });
+    parallel_for(n, [&](int64_t i) {
+        plans[i] = make_plan(tr, net_, leaves[i], counting ? np_ : 0, cprime_, false, !opts_.no_chain_fusion);
+    });
     st_->t_plan_s += now_s() - tp;
     uint64_t stride = 256;
     for (const Plan &pl : plans) {
@@ -625,7 +627,12 @@ std::vector<int32_t> Solver::window_close(int64_t n, bool aggregate) {
         st_->prof_tcount_ms = prof_.tcount_ms;
         st_->prof_tcount_ops = prof_.tcount_ops;
         st_->prof_tcount_launches = prof_.tcount_launches;
+        st_->prof_chain_ms = prof_.chain_ms;
+        st_->prof_chain_bytes = prof_.chain_bytes;
+        st_->prof_chain_launches = prof_.chain_launches;
     }
+    st_->chains += rs.chains;
+    st_->chained_steps += rs.chained_steps;
     st_->kernel_ms += ms;
     st_->t_device_s += now_s() - win_.tw;
     st_->launches += rs.launches;
@@ -777,7 +784,16 @@ int64_t Solver::incumbent_learned() {
     return best;
 }
 
-void Solver::run_bbtn() { search(false, nullptr); }
+void Solver::run_bbtn() {
+    // a network that already fits the space cap is its own only leaf: contract it once
+    // with counts (the value-only pass would only repeat the same contraction)
+    if (overflow_of(tree_, fx0_, opts_.space_cap_log2).sc <= opts_.space_cap_log2) {
+        st_->nodes++;
+        contract_leaves({fx0_});
+        return;
+    }
+    search(false, nullptr);
+}
 
 // The branch-and-bound search over sub-networks. Nodes are expanded depth-first
 // (best child last on the stack); a node whose reference-tree overflow is zero is a
@@ -1092,15 +1108,17 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
         info->bb_leaves = st.leaves;   // the step list below stays that of the root network
         if (c.sc > BBTN_MAX_RANK) return;
     }
-    Plan plan = make_plan(tree_, net_, fx, np_, cprime_, false);
+    Plan plan = make_plan(tree_, net_, fx, np_, cprime_, false, !opts_.no_chain_fusion);
     info->steps = (int64_t)plan.steps.size();
     info->ops = plan.ops;
     info->bytes = plan.bytes;
     info->arena_bytes = (double)plan.arena_bytes;
+    info->chains = (int)plan.chains;
+    info->chained_steps = (int)plan.chained_steps;
     if (dump_path) {
         FILE *f = fopen(dump_path, "w");
         if (!f) fail(BBTN_EIO, std::string("cannot write ") + dump_path);
-        fprintf(f, "rank_a,rank_b,rank_c,summed,low_identity_bits,bytes,ops,nb,nm,nn\n");
+        fprintf(f, "rank_a,rank_b,rank_c,summed,low_identity_bits,bytes,ops,nb,nm,nn,node,a_node,b_node,fused,chain\n");
         for (const PStep &ps : plan.steps) {
             int ra = 0, rb = 0;
             for (int i = 0; i < ps.P.rc; i++) { if (ps.P.oA[i] >= 0) ra++; if (ps.P.oB[i] >= 0) rb++; }
@@ -1113,8 +1131,8 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
                 else if (ps.P.oA[i] >= 0) nm++;
                 else nn++;
             }
-            fprintf(f, "%d,%d,%d,%d,%d,%.0f,%.0f,%d,%d,%d\n", ra, rb, ps.P.rc, ps.P.rs, ident, ps.bytes, ps.ops, nb,
-                    nm, nn);
+            fprintf(f, "%d,%d,%d,%d,%d,%.0f,%.0f,%d,%d,%d,%d,%d,%d,%d,%d\n", ra, rb, ps.P.rc, ps.P.rs, ident, ps.bytes,
+                    ps.ops, nb, nm, nn, ps.node, ps.a_node, ps.b_node, (int)ps.fused, ps.chain_len);
         }
         fclose(f);
     }

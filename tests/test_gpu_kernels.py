@@ -498,3 +498,100 @@ def test_contract_tiled_swapped_operands(P, np_):
     ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
     assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
     _pair_case(P, la, lb, lc, 2, 2300 + np_, lo=-4, hi=4)
+
+
+# ---------------------------------------------------------------- fused chains (K1m)
+
+def _oracle_chain(la, va, steps):
+    """The chain step by step through the oracle's single contraction (values only)."""
+    lab, v = list(la), va
+    for lb, vb, lc in steps:
+        v, _ = oracle.contract(lab, v, np.zeros((0, 1 << len(lab)), np.uint64), lb, vb,
+                               np.zeros((0, 1 << len(lb)), np.uint64), lc, [])
+        lab = list(lc)
+    return v
+
+
+def _random_chain(rng, ra, L, max_sum=3, new_low=False):
+    """A random chain: each step's B holds one or two labels of the current tensor
+    and possibly a new one; some labels are summed (at most max_sum over the chain).
+    Output labels keep the current order with new labels inserted at random places
+    (or at the bottom, new_low) and summed ones dropped."""
+    cur = list(range(ra))
+    nxt = 100
+    steps, summed = [], 0
+    for _ in range(L):
+        k = int(rng.integers(1, 3))
+        lb = [int(x) for x in rng.choice(cur, size=min(k, len(cur)), replace=False)]
+        out = list(cur)
+        if rng.random() < 0.5:
+            lb.append(nxt)
+            pos = 0 if new_low else int(rng.integers(0, len(out) + 1))
+            out.insert(pos, nxt)
+            nxt += 1
+        rng.shuffle(lb)
+        if summed < max_sum and rng.random() < 0.4 and len(out) > 3:
+            drop = lb[int(rng.integers(0, len(lb)))]
+            out.remove(drop)
+            summed += 1
+        vb = rng.integers(-4, 5, size=1 << len(lb)).astype(np.int32)
+        if rng.random() < 0.3:
+            vb[int(rng.integers(0, len(vb)))] = oracle.NEG          # a hard constraint
+        steps.append((lb, vb, out))
+        cur = out
+    return steps
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_contract_chain_parity(P, seed):
+    """Random chains of 1..8 steps (ranks 6..20, up to three summed labels, new
+    labels, hard constraints): the one-pass kernel equals the step-by-step oracle
+    element by element, infeasible entries included."""
+    rng = np.random.default_rng(1000 + seed)
+    for trial in range(6):
+        ra = int(rng.integers(6, 21))
+        L = int(rng.integers(1, 9))
+        steps = _random_chain(rng, ra, L, max_sum=3 if L <= 2 else 2 if L <= 4 else 1, new_low=trial % 2 == 1)
+        va = rng.integers(-6, 7, size=1 << ra).astype(np.int32)
+        va[rng.random(1 << ra) < 0.1] = oracle.NEG
+        want = _oracle_chain(list(range(ra)), va, steps)
+        dsteps = [(lb, torch.from_numpy(vb).cuda(), lc) for lb, vb, lc in steps]
+        got = P.contract_chain(list(range(ra)), torch.from_numpy(va).cuda(), dsteps)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy(), want), (seed, trial, L)
+
+
+@pytest.mark.parametrize("offset", [0, 1])
+def test_contract_chain_vector_and_misaligned(P, offset):
+    """Edge matrices added to a rank-18 tensor whose two lowest bits pass through
+    (the 128-bit load and store path), and the same from a misaligned start."""
+    rng = np.random.default_rng(7)
+    ra = 18
+    la = list(range(ra))
+    steps = [([5, 9], rng.integers(-3, 4, 4).astype(np.int32), la),
+             ([9, 12], rng.integers(-3, 4, 4).astype(np.int32), la),
+             ([12, 17], rng.integers(-3, 4, 4).astype(np.int32), [x for x in la if x != 17])]
+    buf = rng.integers(-5, 6, size=(1 << ra) + 4).astype(np.int32)
+    va = buf[offset:offset + (1 << ra)]
+    want = _oracle_chain(la, va, steps)
+    dbuf = torch.from_numpy(buf).cuda()
+    out = torch.empty((1 << (ra - 1)) + 4, dtype=torch.int32, device="cuda")
+    dsteps = [(lb, torch.from_numpy(vb).cuda(), lc) for lb, vb, lc in steps]
+    got = P.contract_chain(la, dbuf[offset:offset + (1 << ra)], dsteps, out=out[offset:offset + (1 << (ra - 1))])
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+def test_contract_chain_smallest_and_positive_after_neg(P):
+    """Rank-2 results; a positive B entry after a hard constraint (the floor at
+    NEG is applied after every step, so NEG + 4 stays NEG + 4, not NEG)."""
+    la = [0, 1, 2]
+    va = np.array([oracle.NEG, 3, -2, oracle.NEG, 0, 1, 5, -7], np.int32)
+    steps = [([0], np.array([-1, 2], np.int32), [1, 2, 0]),
+             ([1, 7], np.array([4, oracle.NEG, 3, 1], np.int32), [2, 7, 1]),
+             ([2], np.array([4, 4], np.int32), [7, 1])]
+    want = _oracle_chain(la, va, steps)
+    dsteps = [(lb, torch.from_numpy(vb).cuda(), lc) for lb, vb, lc in steps]
+    got = P.contract_chain(la, torch.from_numpy(va).cuda(), dsteps)
+    torch.cuda.synchronize()
+    assert np.array_equal(got.cpu().numpy(), want)

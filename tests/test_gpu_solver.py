@@ -363,3 +363,31 @@ def test_concurrent_contexts_with_a_small_arena_budget(P):
     assert not errors, errors
     for row in rows:
         assert out[row["seed"]] == (row["alpha"], int(row["count"]))
+
+
+@pytest.mark.parametrize("fusion", [True, False])
+def test_chain_fusion_gives_the_oracle_answers(P, fusion):
+    """Fused chains of value-only steps (a frontier tensor absorbing edge matrices in
+    one pass) only change how the value-only leaves run: with fusion on or off the
+    workload instances, a weighted King's subgraph and a lattice with a field give
+    the oracle's answers, and with fusion on the 30x30 value-only leaves do run
+    fused chains."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"]
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, chain_fusion=fusion)
+    chains = 0
+    for row in (rows[0], rows[6], rows[13]):
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+        res = s.solve(inst, count=True, config=True)
+        _check(inst, res, row["alpha"], int(row["count"]))
+        chains += res.stats["chains"]
+    assert (chains > 0) == fusion
+    for inst, cap in ((synth.kings_subgraph(14, 0.8, seed=8, weights="uniform10"), 10),
+                      (synth.square_lattice(12, seed=3, h2=1), 8)):
+        opt, cnt = oracle.solve(inst)
+        for mode in (P.MODE_SLICED, P.MODE_BBTN):
+            r = P.Solver(mode=mode, space_cap_log2=cap, chain_fusion=fusion).solve(inst, count=True, config=True)
+            _check(inst, r, opt, cnt)
+        # values only: every leaf value-only, fused where chains exist
+        r = P.Solver(mode=P.MODE_SLICED, space_cap_log2=cap, chain_fusion=fusion).solve(inst, count=False)
+        assert (r.energy2 if inst.kind == "spin" else r.alpha) == opt

@@ -263,3 +263,29 @@ def test_plane_moduli_rejected_before_any_device_work(P, which):
     assert rc == P._lib.EINVAL and (b"modul" in err or b"prime" in err), err
     for fn in (lib.bbtn_aggregate, lib.bbtn_aggregate_noalloc):
         assert fn(4, fake, fake, 2, primes, fake, fake, None) == P._lib.EINVAL
+
+
+def test_contract_chain_rejects_what_the_kernel_cannot_run(P):
+    """The fused-chain entry point refuses chains outside the kernel's limits with
+    BBTN_EINVAL before touching any buffer (the pointers here are never used)."""
+    lib = P._lib.load()
+    fake = C.c_void_p(0x1000)
+
+    def call(la, steps, L=None):
+        L = len(steps) if L is None else L
+        rb = P.i32_array([len(s[0]) for s in steps])
+        rc = P.i32_array([len(s[1]) for s in steps])
+        lb = P.i32_array([x for s in steps for x in s[0]])
+        lc = P.i32_array([x for s in steps for x in s[1]])
+        vbs = (C.c_void_p * max(len(steps), 1))(*([0x2000] * len(steps)))
+        return lib.bbtn_contract_chain(len(la), P.i32_array(la), fake, L, rb, lb, vbs, rc, lc, fake, None)
+
+    la = list(range(8))
+    ok_step = ([0, 1], la)
+    assert call(la, [ok_step] * 9) == P._lib.EINVAL                          # more than 8 steps
+    assert call(la, [([0, 1, 2, 3, 4], la)]) == P._lib.EINVAL                # B of rank 5
+    four_sums = [([0], la[1:]), ([1], la[2:]), ([2], la[3:]), ([3], la[4:])]
+    assert call(la, four_sums) == P._lib.EINVAL                              # 4 summed labels
+    assert call(la, [([0], la + [50])]) == P._lib.EINVAL                     # output label from nowhere
+    assert call(la, [([0], [0])]) == P._lib.EINVAL                           # result of rank 1
+    assert "chain" in lib.bbtn_last_error().decode()
