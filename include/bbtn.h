@@ -355,6 +355,52 @@ int bbtn_load_file(bbtn_ctx *ctx, const char *path);
  */
 int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config);
 
+/*
+ * Branch sharding across ranks (one process per GPU). The paper's final result is
+ * the counting sum of the contractions of each branch (BBTN section), and the
+ * leaves are independent sub-networks, so `world` ranks can split one instance's
+ * leaves. Every rank loads the same instance into a context with the same options
+ * (BBTN mode) and runs:
+ *  1. bbtn_shard_values(ctx, rank, world, want_count, &local_max): expands the
+ *     search tree on the host (only the heuristic incumbent prunes, so every rank
+ *     gets the same leaf list) and contracts, values only, the leaves i with
+ *     i mod world == rank. *local_max: the largest leaf maximum of this rank, in the
+ *     library's max-plus convention (-2H for spin glasses, alpha for MWIS), or
+ *     BBTN_NEG if none of its leaves is feasible.
+ *  2. the caller takes global_max = the maximum of local_max over the ranks (one
+ *     all-reduce);
+ *  3. bbtn_shard_counts(ctx, global_max, want_config, ...): contracts with counts
+ *     this rank's leaves whose maximum equals global_max and returns this rank's
+ *     part of the counting sum: *value = global_max if it holds such a leaf, else
+ *     BBTN_NEG; planes[t] (host uint64[*np]) its count in plane t, modulo moduli[t]
+ *     (a pair word q1 << 32 | q0 or a 61-bit prime, as for bbtn_contract; the
+ *     spin-flip factor already applied), zero with BBTN_NEG; *n_crt_planes planes
+ *     enter the CRT, a further one (if *np is larger) is the overflow check. With
+ *     want_config and an optimal leaf on this rank, config (host int8[n]) receives an
+ *     optimal configuration (+-1 or 0/1) and *have_config = 1, else 0. Arrays of
+ *     BBTN_MAX_PRIMES + 1 entries always suffice.
+ *  4. the caller combines the ranks' (value, planes) by the counting sum
+ *     (bbtn_aggregate over the gathered results, all with the same moduli) and turns
+ *     the combined planes into the decimal count with bbtn_count_decimal.
+ * With world == 1 this gives bbtn_solve's energy and count (a search whose leaves
+ * are fixed in advance may contract more leaves than bbtn_solve, never fewer
+ * optimal ones). The context holds the rank's leaf list between steps 1 and 3;
+ * any other solve on it in between discards it (BBTN_ESTATE from step 3).
+ */
+int bbtn_shard_values(bbtn_ctx *ctx, int rank, int world, int want_count, int64_t *local_max);
+int bbtn_shard_counts(bbtn_ctx *ctx, int64_t global_max, int want_config, int32_t *value, uint64_t *planes,
+                      uint64_t *moduli, int *np, int *n_crt_planes, int8_t *config, int *have_config);
+
+/*
+ * The exact degeneracy from np count-plane words (host): residues modulo the
+ * planes' moduli (pair words split into their two residues), Garner CRT of the
+ * first n_crt_planes planes into a decimal string (buf, cap; *needed = strlen + 1,
+ * buf may be NULL to query). A further plane is the overflow check: if its
+ * residues disagree with the CRT result, BBTN_EOVERFLOW. Host only.
+ */
+int bbtn_count_decimal(int np, int n_crt_planes, const uint64_t *planes, const uint64_t *moduli, char *buf,
+                       size_t cap, size_t *needed);
+
 /* 2*H* for a spin glass (so that half-integer fields stay integral); alpha for MWIS. */
 int bbtn_get_energy(bbtn_ctx *ctx, int64_t *e);
 

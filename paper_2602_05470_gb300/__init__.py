@@ -326,3 +326,85 @@ class Solver:
         return Result(self._kind, e.value if spin else None, None if spin else e.value, cnt,
                       [int(res[i]) for i in range(k.value)], [int(prs[i]) for i in range(k.value)], cfg,
                       st.as_dict())
+
+    # ------------------------------------------------------------ branch sharding
+
+    def shard_values(self, rank: int, world: int, count: bool = True, inst=None) -> int:
+        """Step 1 of branch sharding (bbtn_shard_values): value-only contraction of
+        this rank's leaves; returns the largest leaf maximum (max-plus convention)."""
+        if inst is not None:
+            self.load(inst)
+        m = C.c_int64()
+        check(_lib.load().bbtn_shard_values(self._ctx, rank, world, int(count), C.byref(m)))
+        return m.value
+
+    def shard_counts(self, global_max: int, config: bool = False):
+        """Step 3 (bbtn_shard_counts): this rank's part of the counting sum as
+        (value, planes, moduli, n_crt_planes, config or None)."""
+        lib = _lib.load()
+        v, np_, ncrt, have = C.c_int32(), C.c_int(), C.c_int(), C.c_int()
+        planes, moduli = (C.c_uint64 * (MAX_PRIMES + 1))(), (C.c_uint64 * (MAX_PRIMES + 1))()
+        cfg = (C.c_int8 * self._n)()
+        check(lib.bbtn_shard_counts(self._ctx, int(global_max), int(config), C.byref(v), planes, moduli,
+                                    C.byref(np_), C.byref(ncrt), cfg, C.byref(have)))
+        k = np_.value
+        x = [int(cfg[i]) for i in range(self._n)] if (config and have.value) else None
+        return v.value, [int(planes[t]) for t in range(k)], [int(moduli[t]) for t in range(k)], ncrt.value, x
+
+
+def count_decimal(planes, moduli, n_crt_planes: int) -> int:
+    """Exact count from count-plane words (bbtn_count_decimal: CRT and overflow check)."""
+    lib = _lib.load()
+    need = C.c_size_t()
+    check(lib.bbtn_count_decimal(len(planes), n_crt_planes, u64_array(planes), u64_array(moduli), None, 0,
+                                 C.byref(need)))
+    buf = C.create_string_buffer(need.value)
+    check(lib.bbtn_count_decimal(len(planes), n_crt_planes, u64_array(planes), u64_array(moduli), buf, need.value,
+                                 C.byref(need)))
+    return int(buf.value.decode())
+
+
+def combine_shards(parts, stream=None):
+    """Counting sum of the ranks' partial results [(value, planes, moduli, n_crt), ...]
+    on the device (bbtn_aggregate), then the exact count: (value, count)."""
+    import numpy as np
+    import torch
+    moduli, ncrt = parts[0][2], parts[0][3]
+    vals = torch.tensor([p[0] for p in parts], dtype=torch.int32, device="cuda")
+    if not moduli:
+        ov, _ = aggregate(vals, None, [], stream=stream)
+        return int(ov.cpu()[0]), None
+    words = np.array([p[1] for p in parts], dtype=np.uint64).T.copy()        # [np][world]
+    cnts = torch.from_numpy(words.view(np.int64)).cuda()
+    ov, oc = aggregate(vals, cnts, moduli, stream=stream)
+    torch.cuda.current_stream().synchronize()
+    v = int(ov.cpu()[0])
+    planes = [int(x) for x in oc.cpu().numpy().view(np.uint64)]
+    return v, count_decimal(planes, moduli, ncrt)
+
+
+def solve_sharded(solver, inst, rank: int, world: int, dist=None, count: bool = True, config: bool = False):
+    """One rank's part of a branch-sharded solve: every rank calls this with the same
+    instance and options. The ranks exchange the largest leaf maximum (all-reduce)
+    and their partial counting sums (all-gather) through torch.distributed `dist`
+    (not needed when world == 1), combine them on the device, and return the
+    instance's (optimum, count, configuration or None); the configuration comes from
+    the rank holding an optimal leaf and is shared with the others."""
+    import torch
+    local = solver.shard_values(rank, world, count, inst=inst)
+    g = torch.tensor([local], dtype=torch.int64, device="cuda")
+    if dist is not None and world > 1:
+        dist.all_reduce(g, op=dist.ReduceOp.MAX)
+    gmax = int(g.cpu()[0])
+    if gmax < FINITE_MIN:
+        raise BBTNError(-7, "no feasible configuration")
+    v, planes, moduli, ncrt, x = solver.shard_counts(gmax, config)
+    part = (v, planes, moduli, ncrt, x)
+    parts = [part]
+    if dist is not None and world > 1:
+        parts = [None] * world
+        dist.all_gather_object(parts, part)
+    value, cnt = combine_shards([p[:4] for p in parts])
+    cfg = next((p[4] for p in parts if p[4] is not None), None)
+    opt = -value if inst.kind == "spin" else value
+    return opt, cnt, cfg

@@ -98,6 +98,10 @@ _SIGS = {
     "bbtn_load_file": ([_vp, C.c_char_p], C.c_int),
     "bbtn_solve": ([_vp, C.c_int, C.c_int], C.c_int),
     "bbtn_get_energy": ([_vp, _i64p], C.c_int),
+    "bbtn_shard_values": ([_vp, C.c_int, C.c_int, C.c_int, _i64p], C.c_int),
+    "bbtn_shard_counts": ([_vp, C.c_int64, C.c_int, _i32p, _u64p, _u64p, _P(C.c_int), _P(C.c_int), _i8p,
+                           _P(C.c_int)], C.c_int),
+    "bbtn_count_decimal": ([C.c_int, C.c_int, _u64p, _u64p, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_get_count_residues": ([_vp, _u64p, _u64p, _P(C.c_int)], C.c_int),
     "bbtn_get_count_dec": ([_vp, C.c_char_p, C.c_size_t, _P(C.c_size_t)], C.c_int),
     "bbtn_get_config": ([_vp, _i8p], C.c_int),

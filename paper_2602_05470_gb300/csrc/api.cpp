@@ -28,6 +28,7 @@ struct bbtn_ctx {
     TileTuner tuner;                   // tuned load layouts, kept across solves
     GnnModel *gnn_branch = nullptr;   // borrowed (bbtn_set_gnn)
     GnnModel *gnn_value = nullptr;
+    std::unique_ptr<Solver> shard;     // branch sharding between bbtn_shard_values and bbtn_shard_counts
 };
 
 namespace {
@@ -357,6 +358,7 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
 
 void bbtn_destroy(bbtn_ctx *ctx) {
     if (!ctx) return;
+    ctx->shard.reset();
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     ctx->arena.stream = ctx->stream;
     ctx->arena.release();
@@ -457,6 +459,91 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
             for (size_t u = ctx->out.n_crt; u < ctx->out.res.size(); u++)
                 if (crt_mod(r, p, ctx->out.primes[u]) != ctx->out.res[u])
                     fail(BBTN_EOVERFLOW, "degeneracy exceeds the range of the CRT primes; use more primes");
+        }
+    });
+}
+
+int bbtn_shard_values(bbtn_ctx *ctx, int rank, int world, int want_count, int64_t *local_max) {
+    return guarded([&] {
+        if (!ctx || !local_max) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
+        if (world < 1 || rank < 0 || rank >= world) fail(BBTN_EINVAL, "rank outside 0..world-1");
+        if (ctx->opts.mode != BBTN_MODE_BBTN) fail(BBTN_EINVAL, "branch sharding needs BBTN mode");
+        if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
+        BBTN_CUDA(cudaSetDevice(ctx->device));
+        ctx->solved = false;
+        ctx->shard.reset(new Solver(ctx->opts, ctx->stream, &ctx->arena, &ctx->tuner));
+        ctx->shard->set_gnn(ctx->gnn_branch, ctx->gnn_value);
+        try {
+            *local_max = ctx->shard->shard_values(ctx->prob, rank, world, want_count != 0, &ctx->stats);
+        } catch (...) {
+            ctx->shard.reset();
+            throw;
+        }
+    });
+}
+
+int bbtn_shard_counts(bbtn_ctx *ctx, int64_t global_max, int want_config, int32_t *value, uint64_t *planes,
+                      uint64_t *moduli, int *np, int *n_crt_planes, int8_t *config, int *have_config) {
+    return guarded([&] {
+        if (!ctx || !value || !np || !n_crt_planes) fail(BBTN_EINVAL, "bad arguments");
+        if (!ctx->shard) fail(BBTN_ESTATE, "bbtn_shard_values has not run on this context");
+        if (want_config && (!config || !have_config)) fail(BBTN_EINVAL, "config output missing");
+        BBTN_CUDA(cudaSetDevice(ctx->device));
+        Solver::ShardResult r;
+        try {
+            r = ctx->shard->shard_counts(global_max, want_config != 0);
+        } catch (...) {
+            ctx->shard.reset();
+            throw;
+        }
+        ctx->shard.reset();
+        *value = r.value;
+        *np = (int)r.planes.size();
+        *n_crt_planes = r.n_crt_planes;
+        for (size_t t = 0; t < r.planes.size(); t++) {
+            if (planes) planes[t] = r.planes[t];
+            if (moduli) moduli[t] = r.moduli[t];
+        }
+        if (have_config) *have_config = r.have_x ? 1 : 0;
+        if (r.have_x && config)
+            for (size_t i = 0; i < r.x.size(); i++) config[i] = ctx->prob.kind == kSpin ? (int8_t)(2 * r.x[i] - 1) : r.x[i];
+    });
+}
+
+int bbtn_count_decimal(int np, int n_crt_planes, const uint64_t *planes, const uint64_t *moduli, char *buf,
+                       size_t cap, size_t *needed) {
+    return guarded([&] {
+        if (np < 1 || np > kMaxPlanes || n_crt_planes < 1 || n_crt_planes > np || !planes || !moduli)
+            fail(BBTN_EINVAL, "bad count planes");
+        uint32_t c[kMaxPlanes];
+        plane_moduli(np, moduli, c);   // checks the moduli
+        std::vector<uint64_t> r, p;
+        for (int t = 0; t < np; t++) {
+            if (is_pair(c[t])) {
+                const uint64_t q0 = moduli[t] & 0xffffffffull, q1 = moduli[t] >> 32;
+                const uint64_t lo = planes[t] & 0xffffffffull, hi = planes[t] >> 32;
+                if (lo >= q0 || hi >= q1) fail(BBTN_EINVAL, "residue not below its modulus");
+                r.push_back(lo);
+                p.push_back(q0);
+                r.push_back(hi);
+                p.push_back(q1);
+            } else {
+                if (planes[t] >= moduli[t]) fail(BBTN_EINVAL, "residue not below its modulus");
+                r.push_back(planes[t]);
+                p.push_back(moduli[t]);
+            }
+        }
+        const size_t k = is_pair(c[0]) ? 2 * (size_t)n_crt_planes : (size_t)n_crt_planes;
+        std::vector<uint64_t> rk(r.begin(), r.begin() + k), pk(p.begin(), p.begin() + k);
+        for (size_t u = k; u < r.size(); u++)
+            if (crt_mod(rk, pk, p[u]) != r[u])
+                fail(BBTN_EOVERFLOW, "degeneracy exceeds the range of the CRT primes; use more primes");
+        std::string s = crt_decimal(rk, pk);
+        if (needed) *needed = s.size() + 1;
+        if (buf) {
+            if (cap < s.size() + 1) fail(BBTN_EINVAL, "buffer too small");
+            memcpy(buf, s.c_str(), s.size() + 1);
         }
     });
 }

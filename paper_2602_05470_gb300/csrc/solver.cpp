@@ -1155,6 +1155,108 @@ void Solver::search_leaves(const Problem &p, int64_t max_leaves, std::vector<int
     leaf_log_ = nullptr;
 }
 
+int64_t Solver::shard_values(const Problem &p, int rank, int world, bool want_count, bbtn_stats *st) {
+    if (world < 1 || rank < 0 || rank >= world) fail(BBTN_EINVAL, "shard: rank outside 0..world-1");
+    shard_release();
+    st_ = st;
+    memset(st, 0, sizeof(*st));
+    const double t0 = now_s();
+    setup(p, 1, want_count);
+    shard_open_ = true;
+    // the leaf list of the host-expanded search tree, the same on every rank
+    std::vector<int8_t> flat;
+    leaf_log_ = &flat;
+    leaf_log_max_ = (int64_t)1 << 40;
+    const double tp = now_s();
+    search(true, nullptr);
+    leaf_log_ = nullptr;
+    st_->t_plan_s += now_s() - tp;
+    const int64_t nleaf = (int64_t)flat.size() / std::max(1, p.n);
+    st_->nodes = 0;
+    st_->leaves = 0;
+    shard_leaves_.clear();
+    for (int64_t i = rank; i < nleaf; i += world)
+        shard_leaves_.emplace_back(flat.begin() + i * p.n, flat.begin() + (i + 1) * p.n);
+    shard_vals_.clear();
+    int64_t best = kNeg;
+    const int64_t bs = std::max(1, opts_.batch);
+    for (size_t i0 = 0; i0 < shard_leaves_.size(); i0 += (size_t)bs) {
+        const size_t n = std::min(shard_leaves_.size() - i0, (size_t)bs);
+        std::vector<std::vector<int8_t>> g(shard_leaves_.begin() + i0, shard_leaves_.begin() + i0 + n);
+        std::vector<int32_t> v = contract_leaves(g, false);
+        for (int32_t x : v) {
+            shard_vals_.push_back(x);
+            if (x >= kFiniteMin) best = std::max<int64_t>(best, x);
+        }
+    }
+    st_->leaves = (int64_t)shard_leaves_.size();
+    st_->t_total_s = now_s() - t0;
+    return best;
+}
+
+Solver::ShardResult Solver::shard_counts(int64_t global_max, bool want_config) {
+    if (!shard_open_) fail(BBTN_ESTATE, "shard: values not computed");
+    const double t0 = now_s();
+    ShardResult r;
+    std::vector<std::vector<int8_t>> opt;
+    for (size_t i = 0; i < shard_leaves_.size(); i++)
+        if (global_max >= kFiniteMin && shard_vals_[i] == global_max) opt.push_back(shard_leaves_[i]);
+    const int64_t bs = std::max(1, opts_.batch);
+    for (size_t i0 = 0; i0 < opt.size(); i0 += (size_t)bs) {
+        const size_t n = std::min(opt.size() - i0, (size_t)bs);
+        ensure_buffers((int64_t)n + 1);
+        window_open();
+        std::vector<std::vector<int8_t>> g(opt.begin() + i0, opt.begin() + i0 + n);
+        enqueue_leaves(g, true, nullptr, 1);
+        window_close((int64_t)n, true);
+    }
+    const uint64_t plane = (uint64_t)dcap_ + 1;
+    int32_t v = kNeg;
+    std::vector<uint64_t> w(np_, 0);
+    BBTN_CUDA(cudaMemcpyAsync(&v, d_val_, sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
+    for (int t = 0; t < np_; t++)
+        BBTN_CUDA(cudaMemcpyAsync(&w[t], d_cnt_ + t * plane, sizeof(uint64_t), cudaMemcpyDeviceToHost, stream_));
+    BBTN_CUDA(cudaStreamSynchronize(stream_));
+    if (!opt.empty() && v != global_max) fail(BBTN_ESTATE, "shard: counting pass disagrees with the value pass");
+    r.value = opt.empty() ? kNeg : v;
+    r.n_crt_planes = n_crt_;
+    for (int t = 0; t < np_; t++) {
+        uint64_t word = opt.empty() ? 0 : w[t];
+        // the spin-flip multiplier, applied per residue like the solver's own result
+        if (pair_) {
+            const uint64_t q0 = primes_[2 * t], q1 = primes_[2 * t + 1];
+            const uint64_t lo = mulmod_host(word & 0xffffffffull, mult_ % q0, q0);
+            const uint64_t hi = mulmod_host(word >> 32, mult_ % q1, q1);
+            word = lo | hi << 32;
+            r.moduli.push_back(q0 | q1 << 32);
+        } else {
+            word = mulmod_host(word, mult_ % primes_[t], primes_[t]);
+            r.moduli.push_back(primes_[t]);
+        }
+        r.planes.push_back(word);
+    }
+    st_->leaves += (int64_t)opt.size();
+    if (want_config && !opt.empty()) {
+        best_fx_ = opt[0];
+        best_val_ = global_max;
+        finish(true);
+        r.x = out_.x;
+        r.have_x = true;
+    }
+    st_->t_total_s += now_s() - t0;
+    shard_release();
+    return r;
+}
+
+void Solver::shard_release() {
+    if (!shard_open_) return;
+    release_buffers();
+    net_.release(stream_);
+    shard_leaves_.clear();
+    shard_vals_.clear();
+    shard_open_ = false;
+}
+
 void Solver::branch_samples(const Problem &p, BranchLog *log, bbtn_stats *st) {
     st_ = st;
     memset(st, 0, sizeof(*st));

@@ -44,6 +44,12 @@ class Solver {
         : opts_(o), stream_(s), arena_(arena), tuner_(tuner) {
         prog_.stream = s;
     }
+    ~Solver() {
+        try {
+            shard_release();
+        } catch (...) {
+        }
+    }
     SolveOutput solve(const Problem &p, bool want_count, bool want_config, bbtn_stats *st);
     // host-only planning summary (bbtn_analyze)
     void analyze(const Problem &p, bbtn_plan_info *info, const char *dump_path);
@@ -60,6 +66,24 @@ class Solver {
     void prepare(const Problem &p, bbtn_stats *st);
     // dry search: the fixings of its leaf sub-networks, n per leaf (host only)
     void search_leaves(const Problem &p, int64_t max_leaves, std::vector<int8_t> &fx, bbtn_stats *st);
+
+    // Branch sharding across ranks. Every rank expands the same search tree on the
+    // host (the dry search: only the heuristic incumbent prunes, so the leaf list
+    // does not depend on the rank) and takes the leaves i = rank (mod world).
+    // shard_values contracts them value-only and returns the largest leaf maximum
+    // (kNeg if none is feasible); shard_counts, given the maximum over all ranks,
+    // contracts with counts this rank's leaves that attain it and returns its part
+    // of the counting sum (value kNeg and zero counts if it holds none).
+    int64_t shard_values(const Problem &p, int rank, int world, bool want_count, bbtn_stats *st);
+    struct ShardResult {
+        int32_t value = kNeg;
+        std::vector<uint64_t> planes, moduli;   // one word per count plane (pair or wide form)
+        int n_crt_planes = 0;
+        std::vector<int8_t> x;                  // an optimal configuration, if this rank holds one
+        bool have_x = false;
+    };
+    ShardResult shard_counts(int64_t global_max, bool want_config);
+    void shard_release();
 
   private:
     struct Leafset;
@@ -126,6 +150,10 @@ class Solver {
     std::vector<float> logit_;          // model logits of x_v = 1 at the root
     void ensure_buffers(int64_t n);
     void release_buffers();
+    // branch sharding state (between shard_values and shard_counts)
+    std::vector<std::vector<int8_t>> shard_leaves_;
+    std::vector<int32_t> shard_vals_;
+    bool shard_open_ = false;
 };
 
 }  // namespace bbtn

@@ -391,3 +391,33 @@ def test_chain_fusion_gives_the_oracle_answers(P, fusion):
         # values only: every leaf value-only, fused where chains exist
         r = P.Solver(mode=P.MODE_SLICED, space_cap_log2=cap, chain_fusion=fusion).solve(inst, count=False)
         assert (r.energy2 if inst.kind == "spin" else r.alpha) == opt
+
+
+@pytest.mark.parametrize("world", [1, 2, 3])
+def test_branch_sharding_emulated_ranks(P, world):
+    """Branch sharding with `world` ranks run one after another on this GPU (each
+    rank its own context; no rank waits on another): the ranks' value-only passes,
+    the maximum over them, their counting passes and the device counting sum of
+    their partial results give the stored oracle answers -- a 30 x 30 workload
+    instance with several leaves and a 16 x 16 lattice at cap 2^10 -- and the rank
+    holding an optimal leaf returns an optimal configuration."""
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    cases = [(synth.kings_subgraph(30, 0.8, seed=g["ksg_30x30_f2"][6]["seed"]), 24,
+              g["ksg_30x30_f2"][6]["alpha"], int(g["ksg_30x30_f2"][6]["count"])),
+             (synth.square_lattice(g["spin_large_f6"][0]["L"], seed=g["spin_large_f6"][0]["seed"]), 10,
+              g["spin_large_f6"][0]["e2"], int(g["spin_large_f6"][0]["count"]))]
+    for inst, cap, opt, cnt in cases:
+        ranks = [P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap) for _ in range(world)]
+        local = [s.shard_values(r, world, inst=inst) for r, s in enumerate(ranks)]
+        gmax = max(local)
+        parts = [s.shard_counts(gmax, config=True) for s in ranks]
+        value, count = P.combine_shards([p[:4] for p in parts])
+        assert (-value if inst.kind == "spin" else value, count) == (opt, cnt)
+        cfgs = [p[4] for p in parts if p[4] is not None]
+        assert cfgs
+        res = type("R", (), {"energy2": opt, "alpha": opt, "count": cnt, "residues": [], "primes": [],
+                             "config": cfgs[0]})
+        _check(inst, res, opt, cnt)
+        one, _, _ = P.solve_sharded(ranks[0], inst, 0, 1)
+        assert one == opt
