@@ -310,6 +310,14 @@ typedef struct {
     int64_t prof_chain_launches;
     int64_t chains;          /* K1m chains launched (one per chain and leaf) */
     int64_t chained_steps;   /* pairwise steps those chains replaced */
+    /* configuration recovery (want_config): intermediates the forward kept as checkpoints,
+       intermediates the top-down walk recomputed, the most tensor bytes alive at once, what
+       keeping every intermediate would take, and the byte budget it ran under */
+    int64_t bwd_kept;
+    int64_t bwd_recomputed;
+    double bwd_peak_bytes;
+    double bwd_keep_all_bytes;
+    double bwd_budget_bytes;
 } bbtn_stats;
 
 /* Fill *opts with defaults. */
@@ -432,7 +440,11 @@ typedef struct {
     int64_t bb_leaves;       /* BBTN mode: its leaf sub-networks */
     int chains;              /* fused chains of value-only steps in the step list (values-only plans) */
     int chained_steps;       /* the steps they replace */
-    int reserved[2];
+    int bwd_kept;            /* configuration recovery of the root network under the budget
+                                (opts.arena_budget_mb, else 1 GiB): checkpoints the forward keeps, */
+    int bwd_recomputed;      /* intermediates the walk recomputes, */
+    double bwd_peak_bytes;   /* tensor bytes alive at most, */
+    double bwd_keep_all_bytes; /* and what keeping every intermediate takes */
 } bbtn_plan_info;
 
 /*

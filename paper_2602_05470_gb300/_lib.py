@@ -48,7 +48,9 @@ class Stats(C.Structure):
                 ("prof_tiled16_launches", C.c_int64), ("prof_tcount_ms", C.c_double),
                 ("prof_tcount_ops", C.c_double), ("prof_tcount_launches", C.c_int64), ("slices_run", C.c_int64),
                 ("prof_chain_ms", C.c_double), ("prof_chain_bytes", C.c_double), ("prof_chain_launches", C.c_int64),
-                ("chains", C.c_int64), ("chained_steps", C.c_int64)]
+                ("chains", C.c_int64), ("chained_steps", C.c_int64), ("bwd_kept", C.c_int64),
+                ("bwd_recomputed", C.c_int64), ("bwd_peak_bytes", C.c_double), ("bwd_keep_all_bytes", C.c_double),
+                ("bwd_budget_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}
@@ -58,7 +60,8 @@ class PlanInfo(C.Structure):
     _fields_ = [("tc_log2", C.c_double), ("sc_log2", C.c_int), ("rho", C.c_double),
                 ("slices_log2", C.c_int), ("steps", C.c_int64), ("ops", C.c_double), ("bytes", C.c_double),
                 ("arena_bytes", C.c_double), ("bb_nodes", C.c_int64), ("bb_leaves", C.c_int64),
-                ("chains", C.c_int), ("chained_steps", C.c_int), ("reserved", C.c_int * 2)]
+                ("chains", C.c_int), ("chained_steps", C.c_int), ("bwd_kept", C.c_int), ("bwd_recomputed", C.c_int),
+                ("bwd_peak_bytes", C.c_double), ("bwd_keep_all_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

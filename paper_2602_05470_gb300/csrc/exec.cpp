@@ -323,7 +323,8 @@ static void find_chains(Plan &plan) {
 // its intermediates fitting in shared memory), lays out their shared memory, and
 // assigns arena blocks in execution order: fused results first, then the other
 // steps in post-order, each block released after its last reader is enqueued.
-static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, bool chains, FreeList &fl) {
+static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, bool chains, FreeList &fl,
+                          const std::vector<char> *keep) {
     const int nsteps = (int)plan.steps.size();
     std::vector<char> fus(t.nodes.size(), 0);
     const int S = np == 0 ? 14 : 11;
@@ -428,7 +429,7 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, boo
             if (c < 0 || t.nodes[c].is_leaf() || (side == 1 && !ps.P.hasB)) continue;
             const PStep &cs = plan.steps[plan.node_step[c]];
             (side ? ps.b : ps.a) = cs.c;
-            if (!keep_all) fl.release(cs.c.off, cs.c_block);
+            if (!keep_all || (keep && !(*keep)[c])) fl.release(cs.c.off, cs.c_block);
         }
     }
     plan.arena_bytes = fl.peak;
@@ -495,14 +496,24 @@ static void finalize_plan(Plan &plan, const CTree &t, int np, bool keep_all, boo
     }
 }
 
+static Plan make_plan_impl(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
+                           const uint32_t *cprime, bool keep_all, bool chains, FreeList &fl,
+                           const std::vector<char> *keep);
+
 Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
                const uint32_t *cprime, bool keep_all, bool chains) {
+    FreeList fl;
+    return make_plan_impl(t, net, fx, np, cprime, keep_all, chains, fl, nullptr);
+}
+
+static Plan make_plan_impl(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx, int np,
+                           const uint32_t *cprime, bool keep_all, bool chains, FreeList &fl,
+                           const std::vector<char> *keep) {
     Plan plan;
     plan.np = np;
     plan.node_step.assign(t.nodes.size(), -1);
     plan.node_layout.assign(t.nodes.size(), {});
     std::vector<View> view(t.nodes.size());
-    FreeList fl;
     std::vector<int> order;
     post_order(t, order);
     const uint64_t elem = 4 + 8ull * np;
@@ -654,7 +665,7 @@ Plan make_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_
             view[nd.r].bit_label.clear();
         }
     }
-    finalize_plan(plan, t, np, keep_all, chains, fl);
+    finalize_plan(plan, t, np, keep_all, chains, fl, keep);
     return plan;
 }
 
@@ -943,30 +954,170 @@ void run_plan(const Plan &plan, const DeviceNetwork &net, char *arena, int32_t *
     run_plans({&plan}, net, arena, 0, out_val, out_cnt, out_plane, s, st, prog);
 }
 
-void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net, char *arena,
-                     const int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x,
-                     cudaStream_t s) {
-    x = fx;
-    int64_t *dsel = nullptr;
-    BBTN_CUDA(cudaMalloc(&dsel, 3 * sizeof(int64_t)));
-    struct Item { int node; int64_t sel; };
-    std::vector<Item> stack{{t.root, 0}};
-    try {
-        while (!stack.empty()) {
-            Item it = stack.back();
-            stack.pop_back();
-            const int si = plan.node_step[it.node];
-            if (si < 0) fail(BBTN_ESTATE, "backward: node without a step");
-            const PStep &ps = plan.steps[si];
+namespace {
+
+// The walk of a backward plan for a given checkpoint set, simulated on the host
+// allocator that the forward left behind.
+void plan_walk(BackwardPlan &bp, const CTree &t, const std::vector<char> &keep, FreeList &fl) {
+    const Plan &pl = bp.fwd;
+    const int nn = (int)t.nodes.size();
+    std::vector<char> avail(nn, 0);
+    std::vector<Ref> cur(nn);
+    bp.actions.clear();
+    bp.recomputed = 0;
+    auto internal = [&](int c) { return c >= 0 && !t.nodes[c].is_leaf(); };
+    for (int n = 0; n < nn; n++)
+        if (internal(n) && keep[n] && pl.node_step[n] >= 0) {
+            avail[n] = 1;
+            cur[n] = pl.steps[pl.node_step[n]].c;
+        }
+    auto operand = [&](const PStep &ps, int side) {
+        const int c = side ? ps.b_node : ps.a_node;
+        return internal(c) && c != t.root ? cur[c] : (side ? ps.b : ps.a);
+    };
+    // recompute the segment below c: every unavailable internal node reachable
+    // from c without passing an available one, in post-order
+    std::function<void(int)> recompute = [&](int c) {
+        if (!internal(c) || avail[c]) return;
+        const PStep &ps = pl.steps[pl.node_step[c]];
+        recompute(ps.a_node);
+        if (ps.P.hasB) recompute(ps.b_node);
+        BwdAction ac;
+        ac.kind = 0;
+        ac.node = c;
+        ac.a = operand(ps, 0);
+        if (ps.P.hasB) ac.b = operand(ps, 1);
+        ac.c = ps.c;
+        ac.c.off = fl.alloc(ps.c_block);
+        cur[c] = ac.c;
+        avail[c] = 1;
+        bp.actions.push_back(ac);
+        bp.recomputed++;
+    };
+    std::vector<int> stack{t.root};
+    while (!stack.empty()) {
+        const int n = stack.back();
+        stack.pop_back();
+        const PStep &ps = pl.steps[pl.node_step[n]];
+        if (internal(ps.a_node) && ps.a_node != n) recompute(ps.a_node);
+        if (ps.P.hasB && internal(ps.b_node)) recompute(ps.b_node);
+        BwdAction ac;
+        ac.kind = 1;
+        ac.node = n;
+        ac.a = operand(ps, 0);
+        if (ps.P.hasB) ac.b = operand(ps, 1);
+        ac.c = n == t.root ? ps.c : cur[n];
+        bp.actions.push_back(ac);
+        if (n != t.root) fl.release(cur[n].off, ps.c_block);   // its own backward was its last reader
+        if (ps.P.hasB && internal(ps.b_node)) stack.push_back(ps.b_node);
+        if (internal(ps.a_node) && ps.a_node != n) stack.push_back(ps.a_node);
+    }
+}
+
+}  // namespace
+
+BackwardPlan make_backward_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx,
+                                uint64_t budget) {
+    const int nn = (int)t.nodes.size();
+    std::vector<char> keep(nn, 1);
+    BackwardPlan best;
+    bool have = false;
+    // sizes of the intermediates (values only), from the plan that keeps them all
+    Plan all = make_plan(t, net, fx, 0, nullptr, true, false);
+    std::vector<double> size(nn, 0.0);
+    double largest = 0;
+    for (const PStep &ps : all.steps)
+        if (ps.c.kind == 1) {
+            size[ps.node] = (double)ps.c_block;
+            largest = std::max(largest, size[ps.node]);
+        }
+    // checkpoints for a segment budget S: post-order, a node's segment is itself plus
+    // its children's unkept segments; while it exceeds S the child with the largest
+    // segment becomes a checkpoint. S = infinity keeps everything (no recompute).
+    std::vector<int> order;
+    post_order(t, order);
+    double total = 0;
+    for (double x : size) total += x;
+    // segment sizes from the whole tree (keep everything) down to the largest tensor:
+    // the first plan within the budget recomputes least; else the smallest peak
+    for (double S = INFINITY;; S = std::isinf(S) ? total / 2 : S / 2) {
+        std::vector<double> acc(nn, 0.0);
+        std::fill(keep.begin(), keep.end(), 0);
+        for (int n : order) {
+            if (t.nodes[n].is_leaf()) continue;
+            const int l = t.nodes[n].l, r = t.nodes[n].r;
+            double a = size[n] + acc[l] + acc[r];
+            while (a > S) {
+                const int c = acc[l] >= acc[r] ? l : r;
+                if (acc[c] <= 0) break;
+                keep[c] = 1;
+                a -= acc[c];
+                acc[c] = 0;
+            }
+            acc[n] = a;
+        }
+        if (std::isinf(S))
+            for (int n = 0; n < nn; n++) keep[n] = !t.nodes[n].is_leaf();
+        BackwardPlan bp;
+        FreeList fl;
+        bp.fwd = make_plan_impl(t, net, fx, 0, nullptr, true, false, fl, &keep);
+        plan_walk(bp, t, keep, fl);
+        bp.peak_bytes = (double)fl.peak;
+        bp.keep_all_bytes = (double)all.arena_bytes;
+        bp.kept = 0;
+        for (int n = 0; n < nn; n++) bp.kept += keep[n] && !t.nodes[n].is_leaf() && n != t.root;
+        const bool fits = bp.peak_bytes <= (double)budget;
+        if (!have || fits || bp.peak_bytes < best.peak_bytes) {
+            best = std::move(bp);
+            have = true;
+        }
+        if (fits || S < largest) break;
+    }
+    // the selection array and the split-K scratch after the tensors
+    uint64_t top = align256((uint64_t)best.peak_bytes);
+    best.sel_off = top;
+    top = align256(top + 8ull * (nn + 1));
+    for (const PStep &ps : best.fwd.steps)
+        if (splitk_eligible(ps.P)) best.scratch_bytes = std::max<uint64_t>(best.scratch_bytes, splitk_scratch_bytes(ps.P.rc, 0));
+    best.scratch_off = top;
+    best.arena_bytes = top + best.scratch_bytes;
+    // the forward's own split-K scratch sits at its plan's offset: keep it inside the arena
+    best.arena_bytes = std::max<size_t>(best.arena_bytes, best.fwd.arena_bytes);
+    return best;
+}
+
+void run_backward(const BackwardPlan &bp, const CTree &t, const DeviceNetwork &net, char *arena,
+                  int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x, cudaStream_t s,
+                  RunStats *st, DeviceBuf *prog) {
+    run_plan(bp.fwd, net, arena, root_val, nullptr, 0, s, st, prog);
+    const int nn = (int)t.nodes.size();
+    int64_t *dsel = (int64_t *)(arena + bp.sel_off);
+    BBTN_CUDA(cudaMemsetAsync(dsel, 0xff, 8ull * (nn + 1), s));          // -1: not selected
+    BBTN_CUDA(cudaMemsetAsync(dsel + t.root, 0, 8, s));                   // the root scalar
+    void *scratch = bp.scratch_bytes ? arena + bp.scratch_off : nullptr;
+    for (const BwdAction &ac : bp.actions) {
+        const PStep &ps = bp.fwd.steps[bp.fwd.node_step[ac.node]];
+        ContractParams P = ps.P;
+        fill_operand(P.A, ac.a, net, arena);
+        P.A.unit_counts = ac.a.kind == 0;
+        if (P.hasB) {
+            fill_operand(P.B, ac.b, net, arena);
+            P.B.unit_counts = ac.b.kind == 0;
+        }
+        if (ac.kind == 0) {
+            P.vc = (int32_t *)(arena + ac.c.off);
+            P.cc = nullptr;
+            P.planeC = 1ull << P.rc;
+            int kind = 0;
+            cudaError_t e = launch_contract(P, s, &kind, scratch, bp.scratch_bytes);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("backward recompute: ") + cudaGetErrorString(e));
+        } else {
             BackwardParams B;
-            ContractParams P = ps.P;
-            fill_operand(P.A, ps.a, net, arena);
-            if (P.hasB) fill_operand(P.B, ps.b, net, arena);
             B.va = P.A.val;
             B.vb = P.hasB ? P.B.val : nullptr;
             B.baseA = P.A.base;
             B.baseB = P.hasB ? P.B.base : 0;
-            B.vc = ps.c.kind == 2 ? root_val : (const int32_t *)(arena + ps.c.off);
+            B.vc = ac.c.kind == 2 ? root_val : (const int32_t *)(arena + ac.c.off);
             B.rc = P.rc;
             B.rs = P.rs;
             B.hasB = P.hasB;
@@ -974,31 +1125,24 @@ void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net,
             memcpy(B.oB, P.oB, 32);
             memcpy(B.sA, P.sA, 32);
             memcpy(B.sB, P.sB, 32);
-            BBTN_CUDA(cudaMemcpyAsync(dsel, &it.sel, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-            cudaError_t e = launch_backward(B, 1, dsel, dsel + 1, dsel + 2, s);
+            int64_t *sb = P.hasB && ps.b_node >= 0 ? dsel + ps.b_node : dsel + nn;
+            cudaError_t e = launch_backward(B, 1, dsel + ac.node, dsel + ps.a_node, sb, s);
             if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("backward kernel: ") + cudaGetErrorString(e));
-            int64_t h[3];
-            BBTN_CUDA(cudaMemcpyAsync(h, dsel, sizeof(h), cudaMemcpyDeviceToHost, s));
-            BBTN_CUDA(cudaStreamSynchronize(s));
-            if (h[1] < 0) fail(BBTN_ESTATE, "backward: no maximising assignment (infeasible)");
-            auto handle = [&](int child, const Ref &r, int64_t idx) {
-                if (r.kind == 0) {
-                    // a network tensor: its free bits are variable values
-                    const auto &labs = net.labels[t.nodes[child].leaf];
-                    for (size_t i = 0; i < labs.size(); i++)
-                        if (fx[labs[i]] < 0) x[labs[i]] = (int8_t)((idx >> i) & 1);
-                } else {
-                    stack.push_back({child, idx});
-                }
-            };
-            handle(ps.a_node, ps.a, h[1]);
-            if (ps.P.hasB) handle(ps.b_node, ps.b, h[2]);
         }
-    } catch (...) {
-        cudaFree(dsel);
-        throw;
+        if (st) st->launches++;
     }
-    cudaFree(dsel);
+    std::vector<int64_t> sel(nn + 1);
+    BBTN_CUDA(cudaMemcpyAsync(sel.data(), dsel, 8ull * (nn + 1), cudaMemcpyDeviceToHost, s));
+    BBTN_CUDA(cudaStreamSynchronize(s));
+    x = fx;
+    for (int n = 0; n < nn; n++) {
+        if (!t.nodes[n].is_leaf()) continue;
+        const int64_t idx = sel[n];
+        if (idx < 0) fail(BBTN_ESTATE, "backward: no maximising assignment (infeasible)");
+        const auto &labs = net.labels[t.nodes[n].leaf];
+        for (size_t i = 0; i < labs.size(); i++)
+            if (fx[labs[i]] < 0) x[labs[i]] = (int8_t)((idx >> i) & 1);
+    }
 }
 
 }  // namespace bbtn

@@ -167,11 +167,36 @@ void run_plans(const std::vector<const Plan *> &plans, const DeviceNetwork &net,
                int32_t *out_val, uint64_t *out_cnt, uint64_t out_plane, cudaStream_t s, RunStats *st,
                DeviceBuf *prog);
 
-// Backward walk after run_plan with keep_all: sets x[v] for every free variable
-// (fixed ones copied from fx). Synchronises the stream.
-void backward_config(const Plan &plan, const CTree &t, const DeviceNetwork &net, char *arena,
-                     const int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x,
-                     cudaStream_t s);
+// Configuration recovery (the tropical backward pass) within a device-memory
+// budget. The forward pass keeps only checkpoint intermediates, chosen so that
+// every subtree segment between checkpoints fits a share of the budget; the walk
+// then goes top-down in an order fixed by the tree alone, recomputes a missing
+// child's segment just before the walk needs it, and releases each tensor after
+// its own backward step. Selections stay on the device (one int64 slot per tree
+// node, read and written by the backward kernels), so the whole walk is enqueued
+// without waiting and read back once.
+struct BwdAction {
+    int kind = 0;          // 0: recompute the step of `node`, 1: backward of `node`
+    int node = -1;
+    Ref a, b, c;           // operands and result, arena offsets resolved
+};
+struct BackwardPlan {
+    Plan fwd;              // values-only forward that keeps the checkpoints
+    std::vector<BwdAction> actions;
+    size_t arena_bytes = 0;          // forward and walk peak + selections + split-K scratch
+    uint64_t sel_off = 0;            // byte offset of the selection array (nodes + 1 int64)
+    uint64_t scratch_off = 0, scratch_bytes = 0;
+    int64_t kept = 0, recomputed = 0;
+    double peak_bytes = 0;           // tensor bytes alive at most (forward and walk)
+    double keep_all_bytes = 0;       // what keeping every intermediate takes
+};
+BackwardPlan make_backward_plan(const CTree &t, const DeviceNetwork &net, const std::vector<int8_t> &fx,
+                                uint64_t budget);
+// Runs the forward (root value to root_val) and the walk; sets x[v] for every free
+// variable (fixed ones copied from fx). One synchronisation of the stream, at the end.
+void run_backward(const BackwardPlan &bp, const CTree &t, const DeviceNetwork &net, char *arena,
+                  int32_t *root_val, const std::vector<int8_t> &fx, std::vector<int8_t> &x, cudaStream_t s,
+                  RunStats *st, DeviceBuf *prog);
 
 // Grow-only device arena, allocated and freed in the order of `stream` (the owning
 // solver's), so growing it does not wait for other contexts' work on the device.

@@ -355,7 +355,15 @@ k_backward(const __grid_constant__ BackwardParams P, const int64_t *sel_o, int64
            int64_t *sel_b) {
     __shared__ unsigned long long best_k;
     const int64_t i = blockIdx.x;
-    const uint64_t o = (uint64_t)sel_o[i];
+    const int64_t so = sel_o[i];
+    if (so < 0) {   // the parent step found no maximiser: nothing to select
+        if (threadIdx.x == 0) {
+            sel_a[i] = -1;
+            sel_b[i] = -1;
+        }
+        return;
+    }
+    const uint64_t o = (uint64_t)so;
     uint64_t ao = 0, bo = 0;
     for (int j = 0; j < P.rc; j++)
         if ((o >> j) & 1) {

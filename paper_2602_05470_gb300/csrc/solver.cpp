@@ -1069,14 +1069,23 @@ void Solver::finish(bool want_config) {
     out_.checked = check_;
     if (want_config) {
         if (best_fx_.empty() || best_val_ != v) fail(BBTN_ESTATE, "optimal branch not recorded");
-        Plan plan = make_plan(tree_, net_, best_fx_, 0, cprime_, true);
-        arena_->reserve(plan.arena_bytes);
+        // forward with checkpoints and the top-down walk, within the arena budget
+        const uint64_t budget =
+            opts_.arena_budget_mb > 0 ? (uint64_t)opts_.arena_budget_mb << 20 : arena_budget_;
+        const double tp = now_s();
+        BackwardPlan bp = make_backward_plan(tree_, net_, best_fx_, budget);
+        st_->t_plan_s += now_s() - tp;
+        arena_->reserve(bp.arena_bytes);
         int32_t *root = d_val_ + dcap_;
         RunStats rs;
         rs.tuner = opts_.autotune ? tuner_ : nullptr;
-        run_plan(plan, net_, arena_->ptr, root, nullptr, 0, stream_, &rs, &prog_);
-        backward_config(plan, tree_, net_, arena_->ptr, root, best_fx_, out_.x, stream_);
-        st_->launches += rs.launches + (int64_t)plan.steps.size();
+        run_backward(bp, tree_, net_, arena_->ptr, root, best_fx_, out_.x, stream_, &rs, &prog_);
+        st_->launches += rs.launches;
+        st_->bwd_kept = bp.kept;
+        st_->bwd_recomputed = bp.recomputed;
+        st_->bwd_peak_bytes = bp.peak_bytes;
+        st_->bwd_keep_all_bytes = bp.keep_all_bytes;
+        st_->bwd_budget_bytes = (double)budget;
         for (auto &xv : out_.x) if (xv < 0) xv = 0;   // variables absent from every tensor
         if (objective(*p_, out_.x) != out_.value)
             fail(BBTN_ESTATE, "recovered configuration does not attain the optimum");
@@ -1115,6 +1124,14 @@ void Solver::analyze(const Problem &p, bbtn_plan_info *info, const char *dump_pa
     info->arena_bytes = (double)plan.arena_bytes;
     info->chains = (int)plan.chains;
     info->chained_steps = (int)plan.chained_steps;
+    {
+        const uint64_t budget = opts_.arena_budget_mb > 0 ? (uint64_t)opts_.arena_budget_mb << 20 : 1ull << 30;
+        BackwardPlan bp = make_backward_plan(tree_, net_, fx, budget);
+        info->bwd_kept = (int)bp.kept;
+        info->bwd_recomputed = (int)bp.recomputed;
+        info->bwd_peak_bytes = bp.peak_bytes;
+        info->bwd_keep_all_bytes = bp.keep_all_bytes;
+    }
     if (dump_path) {
         FILE *f = fopen(dump_path, "w");
         if (!f) fail(BBTN_EIO, std::string("cannot write ") + dump_path);

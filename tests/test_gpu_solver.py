@@ -421,3 +421,30 @@ def test_branch_sharding_emulated_ranks(P, world):
         _check(inst, res, opt, cnt)
         one, _, _ = P.solve_sharded(ranks[0], inst, 0, 1)
         assert one == opt
+
+
+@pytest.mark.parametrize("row,cap,mb", [(0, 10, 1), (1, 12, 4), (2, 16, 64)])
+def test_backward_under_a_small_budget(P, row, cap, mb):
+    """Configuration recovery with the intermediates checkpointed under a small byte
+    budget: the forward keeps only a few of them, the walk recomputes the rest, and
+    the configuration still attains the stored oracle energy (16 x 16 and 20 x 20
+    lattices); the most bytes alive at once stay below keeping every intermediate."""
+    with open(GOLDEN) as f:
+        g = json.load(f)["spin_large_f6"][row]
+    inst = synth.square_lattice(g["L"], seed=g["seed"])
+    res = P.Solver(mode=P.MODE_BBTN, space_cap_log2=cap, arena_budget_mb=mb).solve(inst, count=True, config=True)
+    _check(inst, res, g["e2"], int(g["count"]))
+    st = res.stats
+    assert st["bwd_recomputed"] > 0
+    assert st["bwd_peak_bytes"] < st["bwd_keep_all_bytes"]
+
+
+def test_backward_checkpointed_unique_ground_state(P):
+    """With recomputation forced, the unique ground state is still the oracle's."""
+    inst = synth.square_lattice(10, seed=9, dist="uniform", jmax=1000, h2=1)
+    e2, d, cfg = oracle.spin_square_tm(inst, want_config=True)
+    assert d == 1
+    res = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=24, arena_budget_mb=1).solve(inst, count=True, config=True)
+    assert res.energy2 == e2 and res.count == 1
+    assert res.config == [int(x) for x in cfg]
+    assert res.stats["bwd_recomputed"] > 0
