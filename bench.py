@@ -591,12 +591,52 @@ def run_alu_peak(args):
     print(json.dumps(out), flush=True)
 
 
+PERMUTE_CASES = {
+    # name: (rank, permutation (output bit q <- input bit perm[q]), count planes)
+    "permute_tma": (26, list(range(13, 26)) + list(range(13)), 0),          # 8192 x 8192 transpose
+    "permute_tma_count": (24, list(range(12, 24)) + list(range(12)), 4),    # with four count planes
+    "permute_gather": (26, [1, 0] + list(range(2, 26)), 0),                 # a single-bit run at bit 0: K2
+}
+
+
+def run_permute_case(args):
+    """bbtn_permute on a large tensor, timed with CUDA events: algorithmic bytes =
+    every plane read once and written once."""
+    import torch
+    import paper_2602_05470_gb300 as P
+    r, perm, np_ = PERMUTE_CASES[args.kernel_case]
+    vin = torch.randint(-4, 4, (1 << r,), dtype=torch.int32, device="cuda")
+    cin = torch.randint(0, 1 << 29, (np_, 1 << r), dtype=torch.int64, device="cuda") if np_ else None
+    tma = P._lib.load().bbtn_permute_uses_tma(r, P.i32_array(perm), vin.data_ptr(),
+                                              cin.data_ptr() if np_ else None, vin.data_ptr(),
+                                              cin.data_ptr() if np_ else None, np_)
+    for _ in range(max(args.warmup, 1)):
+        P.permute(perm, vin, cin)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = []
+    for _ in range(args.steps):
+        ev[0].record()
+        P.permute(perm, vin, cin)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    t = sorted(ms)[len(ms) // 2]
+    byts = 2 * (4 + 8 * np_) * (1 << r)
+    peak, kind = measured_peaks()
+    print(json.dumps({"kernel_case": args.kernel_case, "tma": bool(tma), "ms_median": t, "algorithmic_bytes": byts,
+                      "gbs": byts / t / 1e6, "hbm_frac": byts / t / 1e6 / peak, "peak_gbs": peak,
+                      "peak_source": kind}), flush=True)
+
+
 def run_kernel_case(args):
     """One representative contraction step through the C ABI, timed with CUDA events."""
     import torch
     import paper_2602_05470_gb300 as P
     if args.kernel_case == "alu_peak":
         return run_alu_peak(args)
+    if args.kernel_case in PERMUTE_CASES:
+        return run_permute_case(args)
     la, lb, lc, np_ = KERNEL_CASES[args.kernel_case]
     v16 = np_ < 0
     np_ = max(np_, 0)
@@ -645,7 +685,7 @@ def run_kernel_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ksg30")
-    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES) + ["alu_peak"], default=None,
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES) + sorted(PERMUTE_CASES) + ["alu_peak"], default=None,
                     help="time one representative contraction step (or the integer-ALU peak) instead of the workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

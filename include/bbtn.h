@@ -131,6 +131,19 @@ int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t 
                  int32_t *vout, uint64_t *cout, int np, void *stream);
 
 /*
+ * 1 if bbtn_permute with these arguments takes the TMA-staged kernel, else 0 (host
+ * only; the pointers are only checked for alignment). That kernel moves tiles with
+ * cp.async.bulk.tensor loads and stores through shared memory; it serves
+ * permutations whose output bits form at most five runs of consecutive input bits
+ * (the run at input bit 0 and the run at output bit 0 at least two bits long), on
+ * 16-byte aligned buffers. bbtn_permute then synchronises `stream` before it
+ * returns, to report a tile wait that gave up as BBTN_ETIMEOUT; other permutations
+ * run the shared-memory gather kernel asynchronously.
+ */
+int bbtn_permute_uses_tma(int r, const int32_t *perm, const void *vin, const void *cin, const void *vout,
+                          const void *cout, int np);
+
+/*
  * Counting-(+) over n scalars (branch aggregation, paper: the final result is
  * the sum of the contractions of each branch): v* = max_b v_b and
  * c*_t = sum over b with v_b == v* of c_{b,t} mod p_t. vals: device int32[n];

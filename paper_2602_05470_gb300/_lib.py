@@ -85,6 +85,7 @@ _SIGS = {
                             C.c_int),
     "bbtn_contract_values16": ([C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, C.c_int, _i32p, _vp, _vp], C.c_int),
     "bbtn_permute": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int, _vp], C.c_int),
+    "bbtn_permute_uses_tma": ([C.c_int, _i32p, _vp, _vp, _vp, _vp, C.c_int], C.c_int),
     "bbtn_search_leaves": ([_vp, C.c_int64, _i8p, _P(C.c_int64)], C.c_int),
     "bbtn_prepare": ([_vp], C.c_int),
     "bbtn_clear_order_cache": ([], C.c_int),

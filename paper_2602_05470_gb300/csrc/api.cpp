@@ -227,6 +227,12 @@ int bbtn_contract_values16(int ra, const int32_t *la, const int32_t *va, int rb,
     return contract_impl(ra, la, va, nullptr, rb, lb, vb, nullptr, rc, lc, vc, nullptr, 0, nullptr, 1, stream);
 }
 
+int bbtn_permute_uses_tma(int r, const int32_t *perm, const void *vin, const void *cin, const void *vout,
+                          const void *cout, int np) {
+    if (r < 0 || r > BBTN_MAX_RANK || np < 0 || np > kMaxPlanes || (r > 0 && !perm)) return 0;
+    return permute_tma_eligible(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np) ? 1 : 0;
+}
+
 int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin, int32_t *vout,
                  uint64_t *cout, int np, void *stream) {
     return guarded([&] {
@@ -237,8 +243,18 @@ int bbtn_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t 
             if (perm[q] < 0 || perm[q] >= r || seen[perm[q]]) fail(BBTN_EINVAL, "perm is not a permutation");
             seen[perm[q]] = true;
         }
-        cudaError_t e = launch_permute(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np,
-                                       (cudaStream_t)stream);
+        cudaStream_t s = (cudaStream_t)stream;
+        if (permute_tma_eligible(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np)) {
+            cudaError_t e = launch_permute_tma(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np, s);
+            if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("permute (TMA): ") + cudaGetErrorString(e));
+            // the tile waits are bounded: read back whether one gave up
+            BBTN_CUDA(cudaStreamSynchronize(s));
+            bool timed_out = false;
+            BBTN_CUDA(permute_tma_timed_out(&timed_out));
+            if (timed_out) fail(BBTN_ETIMEOUT, "permute (TMA): a tile load did not complete");
+            return;
+        }
+        cudaError_t e = launch_permute(r, perm, vin, cin, 1ull << r, vout, cout, 1ull << r, np, s);
         if (e != cudaSuccess) fail(BBTN_ECUDA, std::string("permute: ") + cudaGetErrorString(e));
     });
 }

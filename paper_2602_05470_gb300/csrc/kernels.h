@@ -118,10 +118,19 @@ struct ChainParams {
 // All entries must have the same L (1 <= L <= kChainMaxSteps) and rc >= 2.
 cudaError_t launch_chain_batch(const ChainParams *p, int n, cudaStream_t s);
 
-// out bit q <- in bit perm[q]
+// out bit q <- in bit perm[q] (K2: shared-memory gather kernel)
 cudaError_t launch_permute(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin,
                            uint64_t plane_in, int32_t *vout, uint64_t *cout, uint64_t plane_out,
                            int np, cudaStream_t s);
+// K2t: the same with TMA tile loads and stores, for permutations whose output bits
+// form at most five runs of consecutive input bits (the runs at input bit 0 and at
+// output bit 0 of length 2 or more) on 16-byte aligned buffers.
+bool permute_tma_eligible(int r, const int32_t *perm, const void *vin, const void *cin, uint64_t plane_in,
+                          const void *vout, const void *cout, uint64_t plane_out, int np);
+cudaError_t launch_permute_tma(int r, const int32_t *perm, const int32_t *vin, const uint64_t *cin, uint64_t plane_in,
+                               int32_t *vout, uint64_t *cout, uint64_t plane_out, int np, cudaStream_t s);
+// Whether a K2t block gave up waiting for a tile (and clears the flag). Synchronous.
+cudaError_t permute_tma_timed_out(bool *flag);
 
 // counting-(+) over n scalars (count plane t of the inputs at cnts + t*plane);
 // result count t at out_cnt[t * out_plane]; scratch: aggregate_scratch_bytes(n, np)

@@ -31,8 +31,8 @@ __device__ __forceinline__ uint32_t tab4(const uint32_t (*t)[256], uint32_t o) {
 
 template <bool HASB>
 __device__ __forceinline__ void build_tables(const ContractParams &P, uint32_t (*tA)[256], uint32_t (*tB)[256],
-                                             uint32_t *kA, uint32_t *kB, int ktb) {
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+                                             uint32_t *kA, uint32_t *kB, int ktb, bool out_tables) {
+    for (int i = threadIdx.x; out_tables && i < 4 * 256; i += blockDim.x) {
         const int ch = i >> 8, v = i & 255;
         uint32_t a = 0, b = 0;
 #pragma unroll
@@ -68,6 +68,27 @@ __device__ __forceinline__ void hi_offsets(const ContractParams &P, int ktb, uin
         }
 }
 
+// An operand's offset as a function of the output index, when its output bits form
+// few runs of consecutive bits: sum over runs of ((o >> out) & mask) << in. The
+// per-block byte tables cost as much to build as a mid-size launch's own work
+// (each thread handles one or two output groups), so few-run maps skip them.
+constexpr int kMaxRuns = 6;
+struct BitRuns {
+    int32_t n;                 // runs; -1: too many, use the byte tables
+    uint32_t w[kMaxRuns];      // run i: output start | length << 8 | operand start << 16
+};
+
+__device__ __forceinline__ uint32_t run_off(const BitRuns &r, uint32_t o) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kMaxRuns; i++)
+        if (i < r.n) {
+            const uint32_t w = r.w[i];
+            s += ((o >> (w & 31u)) & ((1u << ((w >> 8) & 31u)) - 1u)) << (w >> 16);
+        }
+    return s;
+}
+
 // The four outputs of a thread differ in two output bits g1 < g2 (the group bits).
 // The host picks output bits that A does not carry when there are any: outputs
 // that differ only there read the same A entries, so A leaves HBM once.
@@ -75,6 +96,7 @@ struct Group4 {
     int8_t g1, g2;     // group bits
     int8_t vecA;       // g = (0, 1) are A's bits 0, 1 and A is 16-byte aligned: one 128-bit load
     int8_t vecC;       // g = (0, 1) and C is 16-byte aligned: one 128-bit store
+    BitRuns ra, rb;    // output bits -> A / B offsets as runs (both n >= 0: no byte tables)
 };
 
 template <int NP, bool HASB, bool PR>
@@ -84,7 +106,8 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
     const int ktb = P.rs < kKTab ? P.rs : kKTab;
     const uint32_t KT = 1u << ktb;
     uint32_t *kA = ktab, *kB = ktab + KT;
-    build_tables<HASB>(P, tA, tB, kA, kB, ktb);
+    const bool runs = gr.ra.n >= 0 && (!HASB || gr.rb.n >= 0);
+    build_tables<HASB>(P, tA, tB, kA, kB, ktb, !runs);
     __syncthreads();
 
     const int g1 = gr.g1, g2 = gr.g2;
@@ -107,8 +130,8 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
         uint32_t o = (uint32_t)q;
         o = ((o >> g1) << (g1 + 1)) | (o & ((1u << g1) - 1u));
         o = ((o >> g2) << (g2 + 1)) | (o & ((1u << g2) - 1u));
-        const uint32_t ao = tab4(tA, o);
-        const uint32_t bo = HASB ? tab4(tB, o) : 0u;
+        const uint32_t ao = runs ? run_off(gr.ra, o) : tab4(tA, o);
+        const uint32_t bo = HASB ? (runs ? run_off(gr.rb, o) : tab4(tB, o)) : 0u;
         int32_t best[4] = {kNeg, kNeg, kNeg, kNeg};
         for (uint32_t hi = 0; hi < nhi; hi++) {
             uint32_t ah = ao, bh = bo;
@@ -235,6 +258,34 @@ __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Ar
 
 // Group bits: output bits that A does not carry first (they would make A be read
 // once per value), then the lowest remaining bits.
+BitRuns runs_of(const int8_t *o, int rc) {
+    BitRuns r;
+    memset(&r, 0, sizeof r);
+    int start[kMaxRuns], in[kMaxRuns], len[kMaxRuns];
+    int prev = -2;
+    for (int i = 0; i < rc; i++) {
+        if (o[i] < 0) {
+            prev = -2;
+            continue;
+        }
+        if (prev >= 0 && i == prev + 1 && o[i] == o[prev] + 1) {
+            len[r.n - 1]++;
+        } else {
+            if (r.n == kMaxRuns) {
+                r.n = -1;
+                return r;
+            }
+            start[r.n] = i;
+            in[r.n] = o[i];
+            len[r.n] = 1;
+            r.n++;
+        }
+        prev = i;
+    }
+    for (int k = 0; k < r.n; k++) r.w[k] = (uint32_t)start[k] | (uint32_t)len[k] << 8 | (uint32_t)in[k] << 16;
+    return r;
+}
+
 Group4 pick_group(const ContractParams &p) {
     int g[2], ng = 0;
     for (int b = 0; b < p.rc && ng < 2; b++)
@@ -248,6 +299,8 @@ Group4 pick_group(const ContractParams &p) {
     const int32_t *a0 = p.A.val + p.A.base;
     r.vecA = low && p.oA[0] == 0 && p.oA[1] == 1 && ((uintptr_t)a0 & 15) == 0;
     r.vecC = low && ((uintptr_t)p.vc & 15) == 0;
+    r.ra = runs_of(p.oA, p.rc);
+    r.rb = runs_of(p.oB, p.rc);
     return r;
 }
 

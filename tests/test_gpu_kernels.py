@@ -595,3 +595,63 @@ def test_contract_chain_smallest_and_positive_after_neg(P):
     got = P.contract_chain(la, torch.from_numpy(va).cuda(), dsteps)
     torch.cuda.synchronize()
     assert np.array_equal(got.cpu().numpy(), want)
+
+
+def _blocks(r, cuts, order):
+    """A permutation made of the input bit ranges split at `cuts`, put in `order`."""
+    edges = [0] + list(cuts) + [r]
+    blocks = [list(range(edges[i], edges[i + 1])) for i in range(len(edges) - 1)]
+    return [b for k in order for b in blocks[k]]
+
+
+TMA_PERMS = [
+    (12, _blocks(12, [6], [1, 0]), 3),                 # transpose of two 6-bit runs
+    (16, _blocks(16, [2, 9, 13], [2, 0, 3, 1]), 3),    # four runs, short ones at both ends
+    (20, _blocks(20, [10], [1, 0]), 0),                # a 1024 x 1024 transpose, values only
+    (18, _blocks(18, [3, 7, 12, 15], [4, 1, 0, 3, 2]), 2),   # five runs
+    (14, _blocks(14, [5], [0, 1]), 3),                 # identity (one run: plain tiled copy)
+    (17, _blocks(17, [4, 11], [0, 2, 1]), 1),          # low run kept in place, upper runs swapped
+    (22, _blocks(22, [2, 20], [2, 1, 0]), 1),          # runs of 2, 18 and 2 bits
+]
+
+
+@pytest.mark.parametrize("case", range(len(TMA_PERMS)))
+def test_permute_tma_parity(P, case):
+    """Permutations the TMA-staged kernel takes (at most five runs of consecutive
+    bits): element-wise equal to the oracle's single-operand contraction with
+    relabelled outputs, value plane and count planes."""
+    r, perm, np_ = TMA_PERMS[case]
+    rng = np.random.default_rng(50 + case)
+    primes = P.primes(max(np_, 1))[:np_]
+    v, c = _rand(rng, r, np_, -5, 5)
+    dv, dc = _dev(v, c)
+    lib = P._lib.load()
+    assert lib.bbtn_permute_uses_tma(r, P.i32_array(perm), dv.data_ptr(), dc.data_ptr() if dc is not None else None,
+                                     dv.data_ptr(), dc.data_ptr() if dc is not None else None, np_) == 1
+    ov_, oc_ = P.permute(perm, dv, dc)
+    torch.cuda.synchronize()
+    la = list(range(r))
+    lc = [perm[q] for q in range(r)]
+    ev, ec = oracle.contract(la, v, c, None, None, None, lc, primes)
+    assert np.array_equal(ov_.cpu().numpy(), ev)
+    if np_:
+        assert np.array_equal(oc_.cpu().numpy().view(np.uint64), ec)
+
+
+def test_permute_tma_declines_what_it_cannot_tile(P):
+    """Six runs, a single-bit run at bit 0, or a misaligned buffer: the
+    shared-memory kernel runs instead (and still matches)."""
+    lib = P._lib.load()
+    buf = torch.zeros(1 << 13, dtype=torch.int32, device="cuda")
+    ptr = buf.data_ptr()
+    six = _blocks(12, [2, 4, 6, 8, 10], [5, 4, 3, 2, 1, 0])
+    assert lib.bbtn_permute_uses_tma(12, P.i32_array(six), ptr, None, ptr, None, 0) == 0
+    lowbit = [0] + [x + 1 for x in _blocks(11, [5], [1, 0])]      # input bit 0 a run of one bit
+    assert lib.bbtn_permute_uses_tma(12, P.i32_array(lowbit), ptr, None, ptr, None, 0) == 0
+    ok = _blocks(12, [6], [1, 0])
+    assert lib.bbtn_permute_uses_tma(12, P.i32_array(ok), ptr + 4, None, ptr, None, 0) == 0
+    v, _ = _rand(np.random.default_rng(3), 12, 0)
+    ov_, _ = P.permute(six, torch.from_numpy(v).cuda(), None)
+    torch.cuda.synchronize()
+    ev, _ = oracle.contract(list(range(12)), v, np.zeros((0, 1 << 12), np.uint64), None, None, None, six, [])
+    assert np.array_equal(ov_.cpu().numpy(), ev)

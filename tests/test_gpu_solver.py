@@ -423,7 +423,7 @@ def test_branch_sharding_emulated_ranks(P, world):
         assert one == opt
 
 
-@pytest.mark.parametrize("row,cap,mb", [(0, 10, 1), (1, 12, 4), (2, 16, 64)])
+@pytest.mark.parametrize("row,cap,mb", [(0, 14, 1), (1, 14, 1), (2, 16, 2)])
 def test_backward_under_a_small_budget(P, row, cap, mb):
     """Configuration recovery with the intermediates checkpointed under a small byte
     budget: the forward keeps only a few of them, the walk recomputes the rest, and
@@ -441,10 +441,55 @@ def test_backward_under_a_small_budget(P, row, cap, mb):
 
 def test_backward_checkpointed_unique_ground_state(P):
     """With recomputation forced, the unique ground state is still the oracle's."""
-    inst = synth.square_lattice(10, seed=9, dist="uniform", jmax=1000, h2=1)
+    inst = synth.square_lattice(12, seed=9, dist="uniform", jmax=1000, h2=1)
     e2, d, cfg = oracle.spin_square_tm(inst, want_config=True)
     assert d == 1
     res = P.Solver(mode=P.MODE_PLAIN, space_cap_log2=24, arena_budget_mb=1).solve(inst, count=True, config=True)
     assert res.energy2 == e2 and res.count == 1
     assert res.config == [int(x) for x in cfg]
     assert res.stats["bwd_recomputed"] > 0
+
+
+def test_field_lattices_20x20_against_the_oracle(P):
+    """The paper's counting setting (h = 0.5 on every spin, 2h = 1 in the library's
+    integer units) on 20 x 20 +-J lattices: branch-and-bound at cap 2^14 gives the
+    stored oracle energy and degeneracy, and a ground state."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["spin_20x20_field_f8"]
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=14)
+    for row in rows:
+        inst = synth.square_lattice(20, seed=row["seed"], h2=row["h2"])
+        res = s.solve(inst, count=True, config=True)
+        _check(inst, res, row["e2"], int(row["count"]))
+        assert res.stats["sc_log2"] <= 14
+
+
+def test_weighted_ksg_30x30_against_the_oracle(P):
+    """Maximum-weight independent sets (weights 1..10, as in the paper's weighted
+    experiments) on 30 x 30 King's subgraphs at cap 2^24: the stored oracle weight
+    and number of optimal sets, and an optimal set."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["mwis_ksg_30x30_w10_f9"]
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24)
+    for row in rows:
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"], weights="uniform10")
+        res = s.solve(inst, count=True, config=True)
+        _check(inst, res, row["alpha"], int(row["count"]))
+
+
+@pytest.mark.parametrize("idx,h2", [(3, 0), (9, 0), (0, 1)])
+def test_spin_32x32_prime_forms_agree(P, idx, h2):
+    """32 x 32 +-J lattices at cap 2^26 (no oracle reaches them): counts as residues
+    mod three 61-bit primes (wide form) and as pairs of 30-bit primes give the same
+    integer and energy; the ground state attains the energy; with no field the
+    count is even (spin-flip symmetry). h2 = 1 is the paper's h = 0.5."""
+    inst = synth.square_lattice(32, seed=synth.config_seed(3, idx), h2=h2)
+    wide = P.Solver(mode=P.MODE_BBTN, space_cap_log2=26, n_primes=3, wide_counts=True).solve(
+        inst, count=True, config=True)
+    pair = P.Solver(mode=P.MODE_BBTN, space_cap_log2=26, n_primes=3).solve(inst, count=True, config=False)
+    assert (wide.energy2, wide.count) == (pair.energy2, pair.count)
+    assert _energy(inst, wide.config) == wide.energy2
+    assert wide.count > 0 and (h2 or wide.count % 2 == 0)
+    assert wide.stats["sc_log2"] <= 26 and pair.stats["sc_log2"] <= 26
+    for r, p in zip(wide.residues, wide.primes):
+        assert r == wide.count % p
