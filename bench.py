@@ -110,6 +110,24 @@ def ncu_traffic():
     return out
 
 
+RATIO_FILE = os.path.join(ROOT, "profiles", "dram_traffic_kernel_cases.md")
+
+
+def ncu_ratios():
+    """DRAM bytes over algorithmic bytes per kernel on the bench's kernel cases (rows
+    '| `kernel` | case | algorithmic MB | read MB | write MB | ratio |')."""
+    out = {}
+    try:
+        import re
+        for line in open(RATIO_FILE):
+            m = re.match(r"\|\s*`([^`]+)`\s*\|.*\|\s*([\d.]+)\s*\|\s*$", line)
+            if m:
+                out[m.group(1)] = float(m.group(2))
+    except OSError:
+        pass
+    return out
+
+
 def measured_peaks():
     """(measured HBM copy GB/s, "measured"), else the recipe's fallback figure."""
     hbm, src = 6800.0, "fallback"
@@ -415,12 +433,19 @@ def run_ours(args, rank, world, local_rank, wl):
     peak, peak_kind = measured_peaks()
     alu, alu_src = alu_peak()
     traffic = ncu_traffic() if not spin else {}
+    ratios = ncu_ratios()
 
     def entry(kernel, ncu_name, bound, ms, work, launches, pk, unit, source, scale, bytes_=None):
         ach = work / (ms * scale) if ms else 0.0
+        per_launch = (bytes_ / max(launches, 1)) if bytes_ else None
+        tr, tsrc = traffic.get(ncu_name), TRAFFIC_SOURCE if ncu_name in traffic else None
+        if tr is None and per_launch and ncu_name in ratios:
+            tr = ratios[ncu_name] * per_launch
+            tsrc = (f"ncu DRAM bytes / algorithmic bytes = {ratios[ncu_name]:.3f} on this kernel's bench case "
+                    "(profiles/dram_traffic_kernel_cases.md), times this workload's algorithmic bytes per launch")
         return {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
-                "traffic": traffic.get(ncu_name), "traffic_source": TRAFFIC_SOURCE if ncu_name in traffic else None,
-                "algorithmic_bytes_per_launch": (bytes_ / max(launches, 1)) if bytes_ else None,
+                "traffic": tr, "traffic_source": tsrc,
+                "algorithmic_bytes_per_launch": per_launch,
                 "kernel": kernel, "launches": int(launches), "avg_launch_us": 1000 * ms / max(launches, 1),
                 "device_ms": ms, "peak_source": source}
 
@@ -599,6 +624,41 @@ PERMUTE_CASES = {
 }
 
 
+CHAIN_CASES = {
+    # name: (rank of A, steps [(B labels, output labels)]) -- a frontier tensor absorbing
+    # four edge matrices (two of them adding and summing a label), as on the workload
+    "chain": (24, [([3, 17], list(range(24))), ([17, 30], list(range(24)) + [30]),
+                   ([5, 30], [x for x in range(24) if x != 5] + [30]), ([9, 21], [x for x in range(24) if x != 5] + [30])]),
+}
+
+
+def run_chain_case(args):
+    """bbtn_contract_chain on a rank-24 tensor, timed with CUDA events: algorithmic
+    bytes = A read once and the result written once."""
+    import torch
+    import paper_2602_05470_gb300 as P
+    ra, steps = CHAIN_CASES[args.kernel_case]
+    va = torch.randint(-4, 4, (1 << ra,), dtype=torch.int32, device="cuda")
+    dsteps = [(lb, torch.randint(-2, 3, (1 << len(lb),), dtype=torch.int32, device="cuda"), lc) for lb, lc in steps]
+    rc = len(steps[-1][1])
+    out = torch.empty(1 << rc, dtype=torch.int32, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        P.contract_chain(list(range(ra)), va, dsteps, out=out)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(args.steps):
+        P.contract_chain(list(range(ra)), va, dsteps, out=out)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    byts = 4 * ((1 << ra) + (1 << rc))
+    peak, kind = measured_peaks()
+    print(json.dumps({"kernel_case": args.kernel_case, "ms": ms, "algorithmic_bytes": byts, "gbs": byts / ms / 1e6,
+                      "hbm_frac": byts / ms / 1e6 / peak, "peak_gbs": peak, "peak_source": kind,
+                      "unfused_steps": len(steps)}), flush=True)
+
+
 def run_permute_case(args):
     """bbtn_permute on a large tensor, timed with CUDA events: algorithmic bytes =
     every plane read once and written once."""
@@ -637,6 +697,8 @@ def run_kernel_case(args):
         return run_alu_peak(args)
     if args.kernel_case in PERMUTE_CASES:
         return run_permute_case(args)
+    if args.kernel_case in CHAIN_CASES:
+        return run_chain_case(args)
     la, lb, lc, np_ = KERNEL_CASES[args.kernel_case]
     v16 = np_ < 0
     np_ = max(np_, 0)
@@ -682,10 +744,77 @@ def run_kernel_case(args):
                       "peak_gbs": peak, "peak_source": kind}), flush=True)
 
 
+def run_scorer(args):
+    """The learned branch scorer against the plain heuristic (its fallback and judge):
+    lookahead training rows from args.scorer_graphs seeded King's subgraphs of 20x20 to
+    24x24 (caps 2^12 to 2^14, host searches in parallel processes, spawned before the
+    first GPU call), training on the GPU by the library's forward / backward / Adam
+    kernels, then held-out 30x30 King's subgraphs at cap 2^16 solved with and without
+    the scorer: leaves of the search, time-to-exact-count (CUDA events around each
+    solve), identical answers."""
+    import numpy as np
+    from paper_2602_05470_gb300 import gnn
+    import synth
+    specs = [("mis", 20 + i % 5, synth.config_seed(4, 2000 + i), 12 + i % 3, 200, 8, 8)
+             for i in range(args.scorer_graphs)]
+    t0 = time.perf_counter()
+    data = [(inst, rows) for inst, rows in gnn.branch_dataset(specs) if rows]
+    t_rows = time.perf_counter() - t0
+    import torch
+    import paper_2602_05470_gb300 as P
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    model = gnn.GNN(seed=3)
+    held = data[-8:]
+    before = gnn.top1_agreement(model, held)
+    t0 = time.perf_counter()
+    losses = gnn.train(model, data[:-8], epochs=args.scorer_epochs, lr=2e-3, rng=np.random.default_rng(0))
+    t_train = time.perf_counter() - t0
+    after = gnn.top1_agreement(model, held)
+    rows = []
+    for idx in range(args.scorer_instances):
+        inst = synth.kings_subgraph(30, 0.8, seed=synth.config_seed(4, 3000 + idx))
+        row = {"instance": idx}
+        for use in (False, True):
+            s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=16, use_gnn=use, stream=stream.cuda_stream)
+            if use:
+                s.set_gnn(branch=model)
+            leaves = s.analyze(inst)["bb_leaves"]
+            P.clear_order_cache()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            r = s.solve(inst, count=True, config=False)
+            eb.record(stream)
+            eb.synchronize()
+            key = "scorer" if use else "heuristic"
+            row[key] = {"leaves_host_search": leaves, "nodes": r.stats["nodes"], "s": ea.elapsed_time(eb) / 1000,
+                        "answer": [r.alpha, str(r.count)]}
+            s.close()
+        if row["scorer"]["answer"] != row["heuristic"]["answer"]:
+            raise AssertionError(f"instance {idx}: the scorer changed the answer")
+        rows.append(row)
+    import math
+    gm = lambda k: math.exp(sum(math.log(r["scorer"][k] / r["heuristic"][k]) for r in rows) / len(rows))
+    print(json.dumps({
+        "kind": "learned branch scorer vs heuristic",
+        "train": {"graphs": len(data) - 8, "graphs_requested": args.scorer_graphs, "sizes": "20x20..24x24 King's subgraphs",
+                  "caps_log2": [12, 13, 14], "rows": sum(len(r) for _, r in data[:-8]), "epochs": args.scorer_epochs,
+                  "rows_host_s": t_rows, "train_gpu_s": t_train, "loss_first_last": [losses[0], losses[-1]],
+                  "top1_agreement_held_out": [before, after]},
+        "eval": {"instances": rows, "workload": "30x30 King's subgraphs (filling 0.8), cap 2^16, exact count",
+                 "leaves_ratio_geomean": gm("leaves_host_search"), "time_ratio_geomean": gm("s")},
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="ksg30")
-    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES) + sorted(PERMUTE_CASES) + ["alu_peak"], default=None,
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["scorer30"], default="ksg30",
+                    help="scorer30: train the learned branch scorer and compare it with the heuristic")
+    ap.add_argument("--scorer-graphs", type=int, default=200)
+    ap.add_argument("--scorer-epochs", type=int, default=20)
+    ap.add_argument("--scorer-instances", type=int, default=6)
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES) + sorted(PERMUTE_CASES) + sorted(CHAIN_CASES) +
+                    ["alu_peak"], default=None,
                     help="time one representative contraction step (or the integer-ALU peak) instead of the workload")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -716,6 +845,8 @@ def main():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.workload == "scorer30":
+        return run_scorer(args)
     wl = WORKLOADS[args.workload]
     if args.kernel_case:
         run_kernel_case(args)
