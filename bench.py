@@ -56,7 +56,7 @@ WORKLOADS = {
         "metric": "time-to-exact-count per instance (KSG 30x30 MIS, BBTN)",
         "name": "mis_kings_subgraph_30x30_filling0.8_cap2^24_bbtn_counting",
         "gen": _ksg30, "n_inst": 32, "cap": 24, "n_primes": 3, "wide": False, "config": False,
-        "per_step": 8, "streams": 3, "golden": "ksg_30x30_f2",
+        "per_step": 8, "streams": 4, "golden": "ksg_30x30_f2",
         "dtype": "int32+u64(two residues mod 2^30-d)", "data": "synthetic (seeded King's subgraphs)",
         "l2": "256 MiB flush between steps; tensors up to 470 MB",
     },
@@ -833,7 +833,7 @@ def main():
     ap.add_argument("--no-check", action="store_true", help="skip the check of every timed instance's answer")
     ap.add_argument("--streams", type=int, default=0,
                     help="solver contexts solving a step's instances concurrently, one CUDA stream and host thread "
-                         "each (0: the workload's default, 3 for ksg30, 2 for spin32)")
+                         "each (0: the workload's default, 4 for ksg30, 2 for spin32)")
     ap.add_argument("--leaf-trials", type=int, default=0,
                     help="annealing trials for the contraction order of each counting leaf (0: the root order)")
     ap.add_argument("--no-chain-fusion", action="store_true",
