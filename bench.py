@@ -486,6 +486,7 @@ def run_ours(args, rank, world, local_rank, wl):
         sample = 0 if not spin else 16
         sl = make_solver(mode=P.MODE_SLICED, slice_sample=sample)
         alone = make_solver()
+        prof_alone = make_solver(profile=True)
         rows = []
         for idx in pick:
             inst = wl["gen"](idx)
@@ -505,16 +506,25 @@ def run_ours(args, rank, world, local_rank, wl):
             if ran == full and (r_sl.energy2 if spin else r_sl.alpha, r_sl.count) != (
                     r_bb.energy2 if spin else r_bb.alpha, r_bb.count):
                 raise AssertionError(f"instance {idx}: sliced and BBTN answers differ")
+            # the same solve once more with every launch timed: the summed kernel time
+            # against the solve's span bounds what fewer or persistent launches could save
+            P.clear_order_cache()
+            rk = prof_alone.solve(inst, count=True, config=wl["config"])
+            kern = rk.stats["prof_ms"] / 1000.0
             rows.append({"instance": idx, "slices_log2": r_sl.stats["slices_log2"], "slices_run": ran,
                          "ttn_s": t_sl * full / ran, "bbtn_alone_s": t_bb,
-                         "speedup": t_sl * full / ran / t_bb})
+                         "speedup": t_sl * full / ran / t_bb, "bbtn_kernels_s": kern,
+                         "device_idle_share": max(0.0, 1.0 - kern / t_bb) if t_bb else None,
+                         "launches": rk.stats["launches"]})
         sl.close()
         alone.close()
+        prof_alone.close()
         import math
         ttn = {"unit": "s/instance", "instances": rows,
                "ttn_mean_s": sum(r["ttn_s"] for r in rows) / len(rows),
                "bbtn_alone_mean_s": sum(r["bbtn_alone_s"] for r in rows) / len(rows),
                "speedup_geomean": math.exp(sum(math.log(r["speedup"]) for r in rows) / len(rows)),
+               "device_idle_share_mean": sum(r["device_idle_share"] or 0.0 for r in rows) / len(rows),
                "estimate": bool(sample),
                "what": "each instance alone on the GPU, its contraction order found inside the timed call: plain "
                        "TTN = the same kernels with dynamic slicing to the same cap, every slice contracted with "
