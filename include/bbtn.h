@@ -406,7 +406,8 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config);
  * With world == 1 this gives bbtn_solve's energy and count (a search whose leaves
  * are fixed in advance may contract more leaves than bbtn_solve, never fewer
  * optimal ones). The context holds the rank's leaf list between steps 1 and 3;
- * any other solve on it in between discards it (BBTN_ESTATE from step 3).
+ * loading an instance or calling bbtn_solve on it in between discards it (step 3 then
+ * returns BBTN_ESTATE).
  */
 int bbtn_shard_values(bbtn_ctx *ctx, int rank, int world, int want_count, int64_t *local_max);
 int bbtn_shard_counts(bbtn_ctx *ctx, int64_t global_max, int want_config, int32_t *value, uint64_t *planes,

@@ -406,6 +406,7 @@ int bbtn_set_workspace(bbtn_ctx *ctx, void *ptr, size_t bytes) {
 static int load_common(bbtn_ctx *ctx, Problem &&p) {
     return guarded([&] {
         validate(p);
+        ctx->shard.reset();   // a new instance discards a branch-sharded solve in progress
         ctx->prob = std::move(p);
         ctx->loaded = true;
         ctx->solved = false;
@@ -451,6 +452,7 @@ int bbtn_load_mwis(bbtn_ctx *ctx, int n, int m, const int32_t *edges, const int3
 int bbtn_load_file(bbtn_ctx *ctx, const char *path) {
     return guarded([&] {
         if (!ctx || !path) fail(BBTN_EINVAL, "bad arguments");
+        ctx->shard.reset();
         ctx->prob = read_problem_file(path);
         ctx->loaded = true;
         ctx->solved = false;
@@ -462,6 +464,7 @@ int bbtn_solve(bbtn_ctx *ctx, int want_count, int want_config) {
         if (!ctx) fail(BBTN_EINVAL, "ctx is NULL");
         if (!ctx->loaded) fail(BBTN_ESTATE, "no instance loaded");
         ctx->solved = false;
+        ctx->shard.reset();   // so is any other solve on the context
         if (ctx->device < 0) fail(BBTN_ECUDA, "no CUDA device available");
         BBTN_CUDA(cudaSetDevice(ctx->device));
         Solver s(ctx->opts, ctx->stream, &ctx->arena, &ctx->tuner);

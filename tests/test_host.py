@@ -289,3 +289,19 @@ def test_contract_chain_rejects_what_the_kernel_cannot_run(P):
     assert call(la, [([0], la + [50])]) == P._lib.EINVAL                     # output label from nowhere
     assert call(la, [([0], [0])]) == P._lib.EINVAL                           # result of rank 1
     assert "chain" in lib.bbtn_last_error().decode()
+
+
+def test_shard_counts_needs_shard_values(P):
+    """bbtn_shard_counts on a context whose leaf list was never built (or was
+    discarded by loading an instance) is an out-of-order call, refused on the host."""
+    lib = P._lib.load()
+    import ctypes as C
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=6)
+    s.load(synth.kings_subgraph(6, 0.8, seed=1))
+    v, npl, ncrt, have = C.c_int32(), C.c_int(), C.c_int(), C.c_int()
+    planes, moduli = (C.c_uint64 * 9)(), (C.c_uint64 * 9)()
+    rc = lib.bbtn_shard_counts(s._ctx, 0, 0, C.byref(v), planes, moduli, C.byref(npl), C.byref(ncrt), None,
+                               C.byref(have))
+    assert rc == P._lib.ESTATE
+    assert b"shard_values" in lib.bbtn_last_error()
+    s.close()
