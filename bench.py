@@ -419,7 +419,8 @@ def run_ours(args, rank, world, local_rank, wl):
     keys = ("prof_ms", "prof_bytes", "prof_ops", "prof_launches", "prof_stream_ms", "prof_stream_bytes",
             "prof_stream_launches", "prof_scount_ms", "prof_scount_bytes", "prof_scount_launches",
             "prof_tiled_ms", "prof_tiled_ops", "prof_tiled_launches", "prof_tiled16_launches", "prof_tcount_ms",
-            "prof_tcount_ops", "prof_tcount_launches", "prof_chain_ms", "prof_chain_bytes", "prof_chain_launches")
+            "prof_tcount_ops", "prof_tcount_launches", "prof_chain_ms", "prof_chain_bytes", "prof_chain_launches",
+            "prof_tiled_bytes", "prof_tcount_bytes")
     pb = {k: 0.0 for k in keys}
     prof_idx = distinct[:args.profile_instances if args.profile_instances >= 0 else (2 if spin else 32)]
     if not args.no_profile_pass:
@@ -449,6 +450,22 @@ def run_ours(args, rank, world, local_rank, wl):
                 "kernel": kernel, "launches": int(launches), "avg_launch_us": 1000 * ms / max(launches, 1),
                 "device_ms": ms, "peak_source": source}
 
+    def tiled_entry(kernel, ncu_name, ms, ops, byts, launches, alu_pk, alu_src):
+        # Roofline of a register-tiled kernel: its arithmetic intensity (tropical ops
+        # per algorithmic byte, summed over its launches) against the ridge point
+        # alu_pk / HBM peak decides which resource bounds it. A counting step's output
+        # carries 36 bytes per entry, so steps with short sums sit left of the ridge.
+        ai = ops / byts if byts else float("inf")
+        ridge = alu_pk * 1e12 / (peak * 1e9)
+        if ai < ridge:
+            e = entry(kernel, ncu_name, "hbm", ms, byts, launches, peak, "GB/s", peak_kind + " HBM copy", 1e6, byts)
+        else:
+            e = entry(kernel, ncu_name, "alu", ms, ops, launches, alu_pk, "T tropical ops/s", alu_src, 1e9)
+        e.update({"intensity_ops_per_byte": ai, "ridge_ops_per_byte": ridge,
+                  "alu_frac": ops / (ms * 1e9) / alu_pk if ms and alu_pk else None,
+                  "hbm_frac": byts / (ms * 1e6) / peak if ms and peak else None})
+        return e
+
     all16 = pb["prof_tiled_launches"] > 0 and pb["prof_tiled16_launches"] == pb["prof_tiled_launches"]
     planes = wl["n_primes"] + 1
     cform = "residue pairs" if not wl["wide"] else "61-bit residues"
@@ -459,16 +476,16 @@ def run_ours(args, rank, world, local_rank, wl):
         entry(f"k_contract4 counting (streaming gather, K1v, {planes} count planes of {cform})",
               "k_contract4<4, 1, 1, 1>", "hbm", pb["prof_scount_ms"], pb["prof_scount_bytes"],
               pb["prof_scount_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6, pb["prof_scount_bytes"]),
-        entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
-              "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", "alu", pb["prof_tiled_ms"],
-              pb["prof_tiled_ops"], pb["prof_tiled_launches"], alu * (2 if all16 else 1), "T tropical ops/s",
-              alu_src + (" x 2 lanes" if all16 else ""), 1e9),
+        tiled_entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
+                    "k_tiled<0, 16, 1, 64, 0>" if all16 else "k_tiled<0, 16, 0, 64, 0>", pb["prof_tiled_ms"],
+                    pb["prof_tiled_ops"], pb["prof_tiled_bytes"], pb["prof_tiled_launches"],
+                    alu * (2 if all16 else 1), alu_src + (" x 2 lanes" if all16 else "")),
         entry("k_chain value-only (fused chains of streaming steps, K1m)", "k_chain", "hbm", pb["prof_chain_ms"],
               pb["prof_chain_bytes"], pb["prof_chain_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6,
               pb["prof_chain_bytes"]),
-        entry(f"k_tiled counting (register-tiled, K1t, {planes} count planes of {cform})", "k_tiled<4, 1, 0, 64, 1>",
-              "alu", pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_launches"], alu,
-              "T tropical ops/s", alu_src + " (ties add modular products on top)", 1e9),
+        tiled_entry(f"k_tiled counting (register-tiled, K1t, {planes} count planes of {cform})",
+                    "k_tiled<4, 1, 0, 64, 1>", pb["prof_tcount_ms"], pb["prof_tcount_ops"], pb["prof_tcount_bytes"],
+                    pb["prof_tcount_launches"], alu, alu_src + " (ties add modular products on top)"),
     ]
     order = sorted(range(len(kernels)), key=lambda i: -kernels[i]["device_ms"])
     dominant = dict(kernels[order[0]])

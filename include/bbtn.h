@@ -61,6 +61,11 @@ const char *bbtn_version(void);
 /* Message of the calling thread's last failure ("" if none). Never NULL. */
 const char *bbtn_last_error(void);
 
+/* Size in bytes of the structures this header declares, so that a binding can check
+ * its own copies of them: which = 0 bbtn_opts, 1 bbtn_stats, 2 bbtn_plan_info.
+ * Returns 0 for any other value. */
+size_t bbtn_struct_size(int which);
+
 /* The first n primes used for count residues, written to primes[0..n-1] (host).
  * p_t = 2^61 - c_t, c_t ascending, each proven prime by deterministic
  * Miller-Rabin at library load. n <= BBTN_MAX_PRIMES + 1 (the last one is the
@@ -331,6 +336,11 @@ typedef struct {
     double bwd_peak_bytes;
     double bwd_keep_all_bytes;
     double bwd_budget_bytes;
+    /* algorithmic bytes of the register-tiled launches (profile mode), value-only and
+       counting steps: with prof_tiled_ops / prof_tcount_ops they give each kernel's
+       arithmetic intensity, which decides whether HBM or the integer pipe bounds it */
+    double prof_tiled_bytes;
+    double prof_tcount_bytes;
 } bbtn_stats;
 
 /* Fill *opts with defaults. */

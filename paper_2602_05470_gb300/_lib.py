@@ -50,7 +50,8 @@ class Stats(C.Structure):
                 ("prof_chain_ms", C.c_double), ("prof_chain_bytes", C.c_double), ("prof_chain_launches", C.c_int64),
                 ("chains", C.c_int64), ("chained_steps", C.c_int64), ("bwd_kept", C.c_int64),
                 ("bwd_recomputed", C.c_int64), ("bwd_peak_bytes", C.c_double), ("bwd_keep_all_bytes", C.c_double),
-                ("bwd_budget_bytes", C.c_double)]
+                ("bwd_budget_bytes", C.c_double), ("prof_tiled_bytes", C.c_double),
+                ("prof_tcount_bytes", C.c_double)]
 
     def as_dict(self):
         return {k: (getattr(self, k) if k != "reserved" else None) for k, _ in self._fields_ if k != "reserved"}

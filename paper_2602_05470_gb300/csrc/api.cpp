@@ -76,6 +76,15 @@ const char *bbtn_version(void) { return "bbtn-gb300 0.1 (sm_103a)"; }
 
 const char *bbtn_last_error(void) { return get_error(); }
 
+size_t bbtn_struct_size(int which) {
+    switch (which) {
+        case 0: return sizeof(bbtn_opts);
+        case 1: return sizeof(bbtn_stats);
+        case 2: return sizeof(bbtn_plan_info);
+        default: return 0;
+    }
+}
+
 int bbtn_primes(int n, uint64_t *primes) {
     return guarded([&] {
         const auto &tab = prime_table();

@@ -127,9 +127,9 @@ void Profiler::collect() {
         launches++;
         if (r.kind == 0 || r.kind == 3) { stream_ms += t; stream_bytes += r.bytes; stream_launches++; }
         if (r.kind == 6) { scount_ms += t; scount_bytes += r.bytes; scount_launches++; }
-        if (r.kind == 2 || r.kind == 4) { tiled_ms += t; tiled_ops += r.ops; tiled_launches++; }
+        if (r.kind == 2 || r.kind == 4) { tiled_ms += t; tiled_ops += r.ops; tiled_bytes += r.bytes; tiled_launches++; }
         if (r.kind == 4) tiled16_launches++;
-        if (r.kind == 5) { tcount_ms += t; tcount_ops += r.ops; tcount_launches++; }
+        if (r.kind == 5) { tcount_ms += t; tcount_ops += r.ops; tcount_bytes += r.bytes; tcount_launches++; }
         if (r.kind == 7) { chain_ms += t; chain_bytes += r.bytes; chain_launches++; }
     }
     recs.clear();

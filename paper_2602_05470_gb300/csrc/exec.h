@@ -108,7 +108,7 @@ struct Profiler {
     double chain_ms = 0, chain_bytes = 0;
     int64_t chain_launches = 0;
     double stream_ms = 0, stream_bytes = 0, scount_ms = 0, scount_bytes = 0;
-    double tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0;
+    double tiled_ms = 0, tiled_ops = 0, tcount_ms = 0, tcount_ops = 0, tiled_bytes = 0, tcount_bytes = 0;
     int64_t stream_launches = 0, scount_launches = 0, tiled_launches = 0, tiled16_launches = 0, tcount_launches = 0;
     cudaEvent_t get();
     void collect();          // after the stream has been synchronised

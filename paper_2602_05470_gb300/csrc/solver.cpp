@@ -626,6 +626,8 @@ std::vector<int32_t> Solver::window_close(int64_t n, bool aggregate) {
         st_->prof_tiled16_launches = prof_.tiled16_launches;
         st_->prof_tcount_ms = prof_.tcount_ms;
         st_->prof_tcount_ops = prof_.tcount_ops;
+        st_->prof_tcount_bytes = prof_.tcount_bytes;
+        st_->prof_tiled_bytes = prof_.tiled_bytes;
         st_->prof_tcount_launches = prof_.tcount_launches;
         st_->prof_chain_ms = prof_.chain_ms;
         st_->prof_chain_bytes = prof_.chain_bytes;

@@ -96,6 +96,8 @@ struct Group4 {
     int8_t g1, g2;     // group bits
     int8_t vecA;       // g = (0, 1) are A's bits 0, 1 and A is 16-byte aligned: one 128-bit load
     int8_t vecC;       // g = (0, 1) and C is 16-byte aligned: one 128-bit store
+    int8_t vecAc;      // vecA, and every count plane of A starts on 16 bytes: two 128-bit loads per plane
+    int8_t vecCc;      // vecC, and every count plane of C starts on 16 bytes: two 128-bit stores per plane
     BitRuns ra, rb;    // output bits -> A / B offsets as runs (both n >= 0: no byte tables)
 };
 
@@ -215,7 +217,6 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
                     }
                 }
             }
-#pragma unroll
             const uint32_t dC[4] = {0u, dC1, dC2, dC3};
 #pragma unroll
             for (int t = 0; t < NP; t++)
@@ -237,8 +238,10 @@ struct S4Args {
     ContractParams p[NB];
 };
 
+// Register caps: five blocks per SM for values only (48 registers), three with up to
+// four count planes, fewer for the wide form's many planes (no spills in any).
 template <int NP, bool HASB, int NB, bool PR>
-__global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Args<NB> args) {
+__global__ void __launch_bounds__(kThr, NP == 0 ? 5 : NP <= 4 ? 3 : NP <= 6 ? 2 : 1) k_contract4(const __grid_constant__ S4Args<NB> args) {
     __shared__ uint32_t tA[4][256];
     __shared__ uint32_t tB[4][256];
     extern __shared__ uint32_t ktab[];
@@ -253,6 +256,106 @@ __global__ void __launch_bounds__(kThr) k_contract4(const __grid_constant__ S4Ar
         __syncthreads();
         contract4_body<NP, HASB, PR>(sP, args.g[e], blockIdx.x - args.blk0[e],
                                  args.blk0[e + 1] - args.blk0[e], tA, tB, ktab);
+    }
+}
+
+// A counting step with no summed label (Eq. (2) with an empty sum: the semiring
+// product of two broadcast operands): value A + B, count cA * cB, one term per
+// output, so there is no maximum to find before the counts can be read. Every load
+// of an output group (values and all count planes) is issued at once, and count
+// words move 16 bytes at a time where the group's four entries are adjacent.
+template <int NP, bool PR>
+__device__ __forceinline__ void outer4_body(const ContractParams &P, const Group4 gr, uint32_t bid, uint32_t nblk) {
+    const int g1 = gr.g1, g2 = gr.g2;
+    const uint32_t dA1 = P.oA[g1] >= 0 ? 1u << P.oA[g1] : 0u, dA2 = P.oA[g2] >= 0 ? 1u << P.oA[g2] : 0u;
+    const uint32_t dB1 = P.oB[g1] >= 0 ? 1u << P.oB[g1] : 0u, dB2 = P.oB[g2] >= 0 ? 1u << P.oB[g2] : 0u;
+    const uint32_t dA[4] = {0u, dA1, dA2, dA1 + dA2}, dB[4] = {0u, dB1, dB2, dB1 + dB2};
+    const uint32_t dC[4] = {0u, 1u << g1, 1u << g2, (1u << g1) + (1u << g2)};
+    const int32_t *__restrict__ va = P.A.val + P.A.base;
+    const int32_t *__restrict__ vb = P.B.val + P.B.base;
+    const uint64_t *__restrict__ ca = P.A.unit_counts ? nullptr : P.A.cnt + P.A.base;
+    const uint64_t *__restrict__ cb = P.B.unit_counts ? nullptr : P.B.cnt + P.B.base;
+    const uint64_t nq = 1ull << (P.rc - 2);
+    const uint64_t stride = (uint64_t)nblk * blockDim.x;
+    for (uint64_t q = (uint64_t)bid * blockDim.x + threadIdx.x; q < nq; q += stride) {
+        uint32_t o = (uint32_t)q;
+        o = ((o >> g1) << (g1 + 1)) | (o & ((1u << g1) - 1u));
+        o = ((o >> g2) << (g2 + 1)) | (o & ((1u << g2) - 1u));
+        const uint32_t ao = run_off(gr.ra, o), bo = run_off(gr.rb, o);
+        int32_t a[4], b[4];
+        uint64_t xa[NP][4], xb[NP][4];
+        if (gr.vecA) {
+            const int4 x = __ldg((const int4 *)(va + ao));
+            a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) a[j] = __ldg(va + ao + dA[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) b[j] = __ldg(vb + bo + dB[j]);
+#pragma unroll
+        for (int t = 0; t < NP; t++) {
+            if (!ca) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) xa[t][j] = rone<PR>();
+            } else if (gr.vecAc) {
+                const ulonglong2 *p2 = (const ulonglong2 *)(ca + (uint64_t)t * P.A.plane + ao);
+                const ulonglong2 u = __ldg(p2), w = __ldg(p2 + 1);
+                xa[t][0] = u.x; xa[t][1] = u.y; xa[t][2] = w.x; xa[t][3] = w.y;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) xa[t][j] = __ldg(ca + (uint64_t)t * P.A.plane + ao + dA[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) xb[t][j] = cb ? __ldg(cb + (uint64_t)t * P.B.plane + bo + dB[j]) : rone<PR>();
+        }
+        int32_t v[4];
+        bool fin[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            v[j] = max(kNeg, a[j] + b[j]);
+            fin[j] = v[j] >= kFiniteMin;
+        }
+        if (gr.vecC) {
+            *(int4 *)(P.vc + o) = make_int4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) P.vc[o + dC[j]] = v[j];
+        }
+#pragma unroll
+        for (int t = 0; t < NP; t++) {
+            const uint32_t c = P.cprime[t];
+            uint64_t r[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                // a unit operand contributes its count 1: the product is the other count
+                const uint64_t w = !ca ? xb[t][j] : !cb ? xa[t][j] : rmul<PR>(xa[t][j], xb[t][j], c);
+                r[j] = fin[j] ? w : 0ull;
+            }
+            uint64_t *dst = P.cc + (uint64_t)t * P.planeC + o;
+            if (gr.vecCc) {
+                ((ulonglong2 *)dst)[0] = make_ulonglong2(r[0], r[1]);
+                ((ulonglong2 *)dst)[1] = make_ulonglong2(r[2], r[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) dst[dC[j]] = r[j];
+            }
+        }
+    }
+}
+
+template <int NP, int NB, bool PR>
+__global__ void __launch_bounds__(kThr, NP <= 3 ? 3 : 2) k_outer4(const __grid_constant__ S4Args<NB> args) {
+    if constexpr (NB == 1) {
+        outer4_body<NP, PR>(args.p[0], args.g[0], blockIdx.x, gridDim.x);
+    } else {
+        __shared__ ContractParams sP;
+        int e = 0;
+        while (e + 1 < args.n && blockIdx.x >= args.blk0[e + 1]) e++;
+        const uint32_t *src = (const uint32_t *)&args.p[e];
+        for (int i = threadIdx.x; i < (int)(sizeof(ContractParams) / 4); i += blockDim.x) ((uint32_t *)&sP)[i] = src[i];
+        __syncthreads();
+        outer4_body<NP, PR>(sP, args.g[e], blockIdx.x - args.blk0[e], args.blk0[e + 1] - args.blk0[e]);
     }
 }
 
@@ -299,6 +402,8 @@ Group4 pick_group(const ContractParams &p) {
     const int32_t *a0 = p.A.val + p.A.base;
     r.vecA = low && p.oA[0] == 0 && p.oA[1] == 1 && ((uintptr_t)a0 & 15) == 0;
     r.vecC = low && ((uintptr_t)p.vc & 15) == 0;
+    r.vecAc = r.vecA && p.A.cnt && ((uintptr_t)(p.A.cnt + p.A.base) & 15) == 0 && (p.A.plane & 1) == 0;
+    r.vecCc = r.vecC && p.cc && ((uintptr_t)p.cc & 15) == 0 && (p.planeC & 1) == 0;
     r.ra = runs_of(p.oA, p.rc);
     r.rb = runs_of(p.oB, p.rc);
     return r;
@@ -324,6 +429,16 @@ cudaError_t launch4(const ContractParams *ps, int n, cudaStream_t s) {
         a.p[i] = p;
     }
     a.blk0[n] = (uint32_t)total;
+    if constexpr (HASB && NP > 0 && NP <= 4) {
+        // counting steps without a summed label take the one-term kernel (offsets
+        // from bit runs: both operands' output bits must form few runs)
+        bool outer = true;
+        for (int i = 0; i < n; i++) outer = outer && ps[i].rs == 0 && a.g[i].ra.n >= 0 && a.g[i].rb.n >= 0;
+        if (outer) {
+            k_outer4<NP, NB, PR><<<(unsigned)total, kThr, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << ktb);
     if (smem > 48 * 1024) {
         cudaError_t e = allow_max_dynamic_smem<k_contract4<NP, HASB, NB, PR>>();

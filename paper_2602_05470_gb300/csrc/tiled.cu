@@ -26,6 +26,15 @@ namespace {
 
 constexpr int TM = 64, TK = 16;   // row tile, summed chunk
 constexpr int kThr = 256;
+// Counting tiles: a thread's four rows / columns spread over the tile (r + 16 i)
+// instead of adjacent (4 r + i). Spread columns read the count tile without bank
+// conflicts and store the results coalesced; spread rows give every warp a share
+// of each row band's ties (the tie work of a chunk varies more between rows than
+// between columns, and the slowest warp sets the chunk's barrier).
+constexpr bool kRowSpread = true, kColSpread = true;
+// Counting tiles: lanes of a warp along rows (16 rows x 2 columns per warp) instead
+// of along columns (2 rows x 16 columns).
+constexpr bool kCountWarpRows = false;
 
 struct Groups {
     int nb, nm, nn, nk;
@@ -131,21 +140,36 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     const uint64_t baseA = P.A.base + deposit(b, G.bA, G.nb);
     const uint64_t baseB = P.B.base + deposit(b, G.bB, G.nb);
     const uint64_t baseC = deposit(b, G.bC, G.nb);
+    // Summed-label tables: table c holds the deposits of k bits 8c..8c+7, and only
+    // its first 2^(bits of k in that byte) entries are ever read (a step with a
+    // 16-long sum needs 16 of the 768), so only those are built.
     for (int i = threadIdx.x; i < 768; i += kThr) {
-        const uint64_t x = (uint64_t)(i & 255) << (8 * (i >> 8));
-        koffA[i] = (uint32_t)deposit(x, G.kA, G.nk);
-        koffB[i] = (uint32_t)deposit(x, G.kB, G.nk);
+        const int c = i >> 8, v = i & 255;
+        const int nbits = min(8, max(0, G.nk - 8 * c));
+        if (v >> nbits) continue;
+        uint32_t a = 0, bb = 0;
+        for (int j = 0; j < nbits; j++)
+            if ((v >> j) & 1) {
+                const int8_t pa = G.kA[8 * c + j], pb = G.kB[8 * c + j];
+                if (pa >= 0) a += 1u << pa;
+                if (pb >= 0) bb += 1u << pb;
+            }
+        koffA[i] = a;
+        koffB[i] = bb;
     }
-    for (int i = threadIdx.x; i < TM; i += kThr) {
-        const uint64_t m = (uint64_t)tm * TM + i;
-        rowA[i] = (uint32_t)deposit(m, G.mA, G.nm);
-        rowC[i] = (uint32_t)deposit(m, G.mC, G.nm);
+    // row and column tables: one deposit per thread (rowA, rowC, colB, colC in
+    // four 64-thread groups) instead of four in the first 64 threads
+    {
+        const int which = threadIdx.x >> 6, i = threadIdx.x & 63;
+        if (which < 2) {
+            const uint64_t m = (uint64_t)tm * TM + i;
+            (which ? rowC : rowA)[i] = (uint32_t)deposit(m, which ? G.mC : G.mA, G.nm);
+        } else if (i < TN) {
+            const uint64_t n = (uint64_t)tn * TN + i;
+            (which == 3 ? colC : colB)[i] = (uint32_t)deposit(n, which == 3 ? G.nC : G.nB, G.nn);
+        }
     }
-    for (int i = threadIdx.x; i < TN; i += kThr) {
-        const uint64_t n = (uint64_t)tn * TN + i;
-        colB[i] = (uint32_t)deposit(n, G.nB, G.nn);
-        colC[i] = (uint32_t)deposit(n, G.nC, G.nn);
-    }
+    static_assert(kThr == 256 && TM == 64, "four 64-thread table groups");
     __syncthreads();
 
     Lanes<4> LA;
@@ -269,6 +293,11 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         // shared-memory stages while the current one is computed. Unit-count operands
         // copy no counts: a maximising entry is finite, so its count is 1.
         typedef CStage<NP, TN> St;
+        const int tx = kCountWarpRows ? (int)(threadIdx.x >> 4) : (int)(threadIdx.x & 15);
+        const int ty = kCountWarpRows ? (int)(threadIdx.x & 15) : (int)(threadIdx.x >> 4);
+        // tile row / column of a thread's output (i, j)
+        auto crow = [](int ty_, int i) { return kRowSpread ? ty_ + 16 * i : ty_ * 4 + i; };
+        auto ccol = [](int tx_, int j) { return MC == 4 && kColSpread ? tx_ + 16 * j : tx_ * MC + j; };
         unsigned char *stage0 = (unsigned char *)(((uintptr_t)(colC + TN) + 15) & ~(uintptr_t)15);
         const bool ua = P.A.unit_counts, ub = P.B.unit_counts;
         const uint64_t one = PR ? 0x100000001ull : 1ull;
@@ -327,10 +356,18 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                 for (int j = 0; j < MC; j++) cm[i][j] = kNeg;
 #pragma unroll
             for (int kk = 0; kk < TK; kk++) {
-                const int4 a4 = *(const int4 *)&cvA[kk][ty * 4];
-                const int a[4] = {a4.x, a4.y, a4.z, a4.w};
-                int bb[MC];
-                if constexpr (MC == 4) {
+                int a[4], bb[MC];
+                if constexpr (kRowSpread) {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) a[i] = cvA[kk][ty + 16 * i];
+                } else {
+                    const int4 a4 = *(const int4 *)&cvA[kk][ty * 4];
+                    a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
+                }
+                if constexpr (MC == 4 && kColSpread) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) bb[j] = cvB[kk][tx + 16 * j];
+                } else if constexpr (MC == 4) {
                     const int4 b4 = *(const int4 *)&cvB[kk][tx * 4];
                     bb[0] = b4.x; bb[1] = b4.y; bb[2] = b4.z; bb[3] = b4.w;
                 } else {
@@ -351,7 +388,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                         for (int t = 0; t < NP; t++) acc[i][j][t] = 0;
                     }
                     if (cm[i][j] == best[i][j] && cm[i][j] >= kFiniteMin) {
-                        const int mi = ty * 4 + i, nj = tx * MC + j;
+                        const int mi = crow(ty, i), nj = ccol(tx, j);
                         if constexpr (PR) {
                             // two residues per word: each half's products are below 2^60,
                             // so the chunk's (at most 16) terms sum in 64 bits exactly
@@ -398,7 +435,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         for (int i = 0; i < 4; i++)
 #pragma unroll
             for (int j = 0; j < MC; j++) {
-                const uint64_t o = baseC + rowC[ty * 4 + i] + colC[tx * MC + j];
+                const uint64_t o = baseC + rowC[crow(ty, i)] + colC[ccol(tx, j)];
                 P.vc[o] = best[i][j];
 #pragma unroll
                 for (int t = 0; t < NP; t++) P.cc[(uint64_t)t * P.planeC + o] = acc[i][j][t];

@@ -655,3 +655,72 @@ def test_permute_tma_declines_what_it_cannot_tile(P):
     torch.cuda.synchronize()
     ev, _ = oracle.contract(list(range(12)), v, np.zeros((0, 1 << 12), np.uint64), None, None, None, six, [])
     assert np.array_equal(ov_.cpu().numpy(), ev)
+
+
+# ---- counting steps with no summed label (one product per output) take their own
+# kernel: 128-bit count-word loads and stores where A's and C's count planes start
+# on 16 bytes and the four outputs of a thread are A's and C's two lowest bits,
+# scalar words otherwise (count tensors offset by one word); unit counts on either
+# side (the product is then the other operand's count).
+OUTER = [
+    # (la, lb, lc)
+    (list(range(14)), [12, 13], list(range(14))),                  # B inside A: vector loads and stores
+    (list(range(14)), [13, 20], list(range(14)) + [20]),           # a B-only label on top
+    (list(range(14)), [0, 20], [20] + list(range(14))),            # a B-only label at C's bit 0
+    ([3, 0, 1, 2] + list(range(4, 14)), [0, 1], list(range(14))),  # A's bits permuted against C's
+    (list(range(15)), [40], list(range(15)) + [40]),               # a vertex-like B on top
+]
+
+
+def _outer_run(P, la, lb, lc, pair, seed, sa=0, sc=0, unitA=False, unitB=False):
+    rng = np.random.default_rng(seed)
+    moduli = P.prime_pairs(4) if pair else P.primes(3)
+    np_ = len(moduli)
+    va = rng.integers(-4, 5, size=1 << len(la)).astype(np.int32)
+    va[rng.random(va.size) < 0.05] = oracle.NEG
+    vb = rng.integers(-4, 5, size=1 << len(lb)).astype(np.int32)
+    vb[rng.random(vb.size) < 0.05] = oracle.NEG
+
+    def planes(v, unit):
+        if unit:
+            one = np.uint64(0x100000001) if pair else np.uint64(1)
+            return np.where(v >= -(1 << 28), one, np.uint64(0))[None, :].repeat(np_, 0)
+        if pair:
+            return _pair_planes(rng, v, moduli)
+        c = np.stack([rng.integers(0, int(m), size=v.size, dtype=np.uint64) for m in moduli])
+        c[:, v < -(1 << 28)] = 0
+        return c
+
+    ca, cb = planes(va, unitA), planes(vb, unitB)
+    # count tensors placed sa / sc words past a 16-byte boundary
+    ca_full = torch.zeros(np_ * va.size + sa, dtype=torch.int64, device="cuda")
+    ca_full[sa:] = torch.from_numpy(ca.reshape(-1).view(np.int64)).cuda()
+    cc_full = torch.zeros(np_ * (1 << len(lc)) + sc, dtype=torch.int64, device="cuda")
+    vc = torch.empty(1 << len(lc), dtype=torch.int32, device="cuda")
+    cc = cc_full[sc:].view(np_, 1 << len(lc))
+    dva, dvb = torch.from_numpy(va).cuda(), torch.from_numpy(vb).cuda()
+    dca = None if unitA else ca_full[sa:].view(np_, va.size)
+    dcb = None if unitB else torch.from_numpy(cb.view(np.int64)).cuda()
+    P.contract(la, dva, dca, lb, dvb, dcb, lc, moduli, out=(vc, cc))
+    torch.cuda.synchronize()
+    if pair:
+        ov, oc = _oracle_pair(la, va, ca, lb, vb, cb, lc, moduli)
+    else:
+        ov, oc = oracle.contract(la, va, ca, lb, vb, cb, lc, moduli)
+    assert np.array_equal(vc.cpu().numpy(), ov)
+    assert np.array_equal(cc.cpu().numpy().view(np.uint64), oc)
+
+
+@pytest.mark.parametrize("case", range(len(OUTER)))
+@pytest.mark.parametrize("form", ["pair", "wide"])
+@pytest.mark.parametrize("shift", [(0, 0), (1, 0), (0, 1)])
+def test_contract_outer_counting(P, case, form, shift):
+    la, lb, lc = OUTER[case]
+    _outer_run(P, la, lb, lc, form == "pair", 2000 + case, sa=shift[0], sc=shift[1])
+
+
+@pytest.mark.parametrize("case", range(len(OUTER)))
+@pytest.mark.parametrize("unit", [(True, False), (False, True), (True, True)])
+def test_contract_outer_unit_counts(P, case, unit):
+    la, lb, lc = OUTER[case]
+    _outer_run(P, la, lb, lc, True, 2100 + case, unitA=unit[0], unitB=unit[1])

@@ -39,6 +39,18 @@ def test_every_declared_symbol_is_exported(P):
     assert not missing, missing
 
 
+def test_binding_structs_match_the_header(P):
+    """The ctypes copies of bbtn_opts, bbtn_stats and bbtn_plan_info have the
+    library's sizes (a field added on one side only would shift every later one)."""
+    lib = P._lib.load()
+    lib.bbtn_struct_size.restype = C.c_size_t
+    lib.bbtn_struct_size.argtypes = [C.c_int]
+    assert lib.bbtn_struct_size(0) == C.sizeof(P._lib.Opts)
+    assert lib.bbtn_struct_size(1) == C.sizeof(P._lib.Stats)
+    assert lib.bbtn_struct_size(2) == C.sizeof(P._lib.PlanInfo)
+    assert lib.bbtn_struct_size(3) == 0
+
+
 def test_version_and_error_strings(P):
     lib = P._lib.load()
     assert b"sm_103a" in lib.bbtn_version()
