@@ -70,9 +70,13 @@ __host__ __device__ __forceinline__ uint32_t pair_d1(uint32_t c) { return (c >> 
 // x mod q for q = 2^30 - d, d < 2^10, any x < 2^64: 2^30 == d (mod q), so
 // x = h 2^30 + l == h d + l; h < 2^34 gives y < 2^44 + 2^30, and folding y once more
 // gives z < 2^30 + 2^25 < 2q, fixed by one conditional subtraction.
-__host__ __device__ __forceinline__ uint32_t reduce64_30(uint64_t x, uint32_t d) {
+__host__ __device__ __forceinline__ uint32_t fold64_30(uint64_t x, uint32_t d) {
     const uint64_t y = (x >> 30) * d + (x & kM30);
-    const uint32_t z = (uint32_t)(y >> 30) * d + (uint32_t)(y & kM30);
+    return (uint32_t)(y >> 30) * d + (uint32_t)(y & kM30);
+}
+
+__host__ __device__ __forceinline__ uint32_t reduce64_30(uint64_t x, uint32_t d) {
+    const uint32_t z = fold64_30(x, d);   // z < 2q, congruent to x
     const uint32_t q = (1u << 30) - d;
     return z >= q ? z - q : z;
 }

@@ -192,25 +192,46 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
                 for (uint32_t k = 0; k < KT; k++) {
                     const uint32_t ea = ah + kA[k];
                     const uint32_t eb = HASB ? bh + kB[k] : 0u;
+                    // which of the four outputs this assignment maximises
+                    bool tie[4];
+                    if (vecA) {
+                        const int4 x = __ldg((const int4 *)(va + ea));
+                        const int32_t av[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        if (best[j] < kFiniteMin) continue;
-                        const uint32_t ej = ea + dA[j];
-                        const int32_t av = __ldg(va + ej);
-                        const int32_t bv = HASB ? __ldg(vb + eb + dB[j]) : 0;
-                        if (av + bv != best[j]) continue;
+                        for (int j = 0; j < 4; j++)
+                            tie[j] = best[j] >= kFiniteMin && av[j] + (HASB ? __ldg(vb + eb + dB[j]) : 0) == best[j];
+                    } else {
 #pragma unroll
-                        for (int t = 0; t < NP; t++) {
-                            const uint32_t c = P.cprime[t];
-                            uint64_t term;
-                            if (P.A.unit_counts) {
-                                term = (HASB && !P.B.unit_counts)
-                                           ? __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j])
-                                           : rone<PR>();
-                            } else {
-                                const uint64_t x = __ldg(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ej);
-                                if (!HASB || P.B.unit_counts) term = x;
-                                else term = rmul<PR>(x, __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]), c);
+                        for (int j = 0; j < 4; j++)
+                            tie[j] = best[j] >= kFiniteMin &&
+                                     __ldg(va + ea + dA[j]) + (HASB ? __ldg(vb + eb + dB[j]) : 0) == best[j];
+                    }
+                    if (!(tie[0] || tie[1] || tie[2] || tie[3])) continue;
+#pragma unroll
+                    for (int t = 0; t < NP; t++) {
+                        const uint32_t c = P.cprime[t];
+                        // A's count words of the four outputs: two 128-bit loads when they
+                        // are adjacent and aligned, else the tied ones one by one
+                        uint64_t xa[4];
+                        if (P.A.unit_counts) {
+#pragma unroll
+                            for (int j = 0; j < 4; j++) xa[j] = rone<PR>();
+                        } else if (gr.vecAc) {
+                            const ulonglong2 *p2 = (const ulonglong2 *)(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ea);
+                            const ulonglong2 u = __ldg(p2), w = __ldg(p2 + 1);
+                            xa[0] = u.x; xa[1] = u.y; xa[2] = w.x; xa[3] = w.y;
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; j++)
+                                xa[j] = tie[j] ? __ldg(P.A.cnt + (uint64_t)t * P.A.plane + P.A.base + ea + dA[j]) : 0ull;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            if (!tie[j]) continue;
+                            uint64_t term = xa[j];
+                            if (HASB && !P.B.unit_counts) {
+                                const uint64_t y = __ldg(P.B.cnt + (uint64_t)t * P.B.plane + P.B.base + eb + dB[j]);
+                                term = P.A.unit_counts ? y : rmul<PR>(term, y, c);
                             }
                             acc[j][t] = radd<PR>(acc[j][t], term, c);
                         }
@@ -219,9 +240,16 @@ __device__ __forceinline__ void contract4_body(const ContractParams &P, const Gr
             }
             const uint32_t dC[4] = {0u, dC1, dC2, dC3};
 #pragma unroll
-            for (int t = 0; t < NP; t++)
+            for (int t = 0; t < NP; t++) {
+                uint64_t *dst = P.cc + (uint64_t)t * P.planeC + o;
+                if (gr.vecCc) {   // the four count words adjacent and 16-byte aligned
+                    ((ulonglong2 *)dst)[0] = make_ulonglong2(acc[0][t], acc[1][t]);
+                    ((ulonglong2 *)dst)[1] = make_ulonglong2(acc[2][t], acc[3][t]);
+                } else {
 #pragma unroll
-                for (int j = 0; j < 4; j++) P.cc[(uint64_t)t * P.planeC + o + dC[j]] = acc[j][t];
+                    for (int j = 0; j < 4; j++) dst[dC[j]] = acc[j][t];
+                }
+            }
         }
     }
 }

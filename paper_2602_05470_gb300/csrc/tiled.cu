@@ -34,7 +34,7 @@ constexpr int kThr = 256;
 constexpr bool kRowSpread = true, kColSpread = true;
 // Counting tiles: lanes of a warp along rows (16 rows x 2 columns per warp) instead
 // of along columns (2 rows x 16 columns).
-constexpr bool kCountWarpRows = false;
+constexpr bool kCountWarpRows = true;
 
 struct Groups {
     int nb, nm, nn, nk;
@@ -390,11 +390,17 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                     if (cm[i][j] == best[i][j] && cm[i][j] >= kFiniteMin) {
                         const int mi = crow(ty, i), nj = ccol(tx, j);
                         if constexpr (PR) {
-                            // two residues per word: each half's products are below 2^60,
-                            // so the chunk's (at most 16) terms sum in 64 bits exactly
+                            // Two residues per word, each accumulated below 2q < 2^31 (not
+                            // canonical until the store). A chunk's sum starts from the
+                            // accumulator: 16 products below q^2 = (2^30 - d)^2 add up to
+                            // under 2^64 - 2^35 d, so with the accumulator it stays exact in
+                            // 64 bits, and one fold (no subtraction) brings it below 2q.
                             uint64_t s0[NP], s1[NP];
 #pragma unroll
-                            for (int t = 0; t < NP; t++) s0[t] = s1[t] = 0;
+                            for (int t = 0; t < NP; t++) {
+                                s0[t] = (uint32_t)acc[i][j][t];
+                                s1[t] = acc[i][j][t] >> 32;
+                            }
                             for (int kk = 0; kk < TK; kk++) {
                                 if (cvA[kk][mi] + cvB[kk][nj] != cm[i][j]) continue;
 #pragma unroll
@@ -407,9 +413,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
 #pragma unroll
                             for (int t = 0; t < NP; t++) {
                                 const uint32_t c = P.cprime[t];
-                                const uint64_t w = (uint64_t)reduce64_30(s1[t], pair_d1(c)) << 32 |
-                                                   reduce64_30(s0[t], pair_d0(c));
-                                acc[i][j][t] = addmod_pair(acc[i][j][t], w, c);
+                                acc[i][j][t] = (uint64_t)fold64_30(s1[t], pair_d1(c)) << 32 | fold64_30(s0[t], pair_d0(c));
                             }
                         } else {
                             u128 part[NP];
@@ -438,7 +442,18 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                 const uint64_t o = baseC + rowC[crow(ty, i)] + colC[ccol(tx, j)];
                 P.vc[o] = best[i][j];
 #pragma unroll
-                for (int t = 0; t < NP; t++) P.cc[(uint64_t)t * P.planeC + o] = acc[i][j][t];
+                for (int t = 0; t < NP; t++) {
+                    uint64_t w = acc[i][j][t];
+                    if constexpr (PR) {   // the accumulated halves are below 2q: one subtraction each
+                        const uint32_t c = P.cprime[t];
+                        const uint32_t q0 = (1u << 30) - pair_d0(c), q1 = (1u << 30) - pair_d1(c);
+                        uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+                        lo = lo >= q0 ? lo - q0 : lo;
+                        hi = hi >= q1 ? hi - q1 : hi;
+                        w = (uint64_t)hi << 32 | lo;
+                    }
+                    P.cc[(uint64_t)t * P.planeC + o] = w;
+                }
             }
     }
 }

@@ -672,14 +672,14 @@ OUTER = [
 ]
 
 
-def _outer_run(P, la, lb, lc, pair, seed, sa=0, sc=0, unitA=False, unitB=False):
+def _outer_run(P, la, lb, lc, pair, seed, sa=0, sc=0, unitA=False, unitB=False, neg=0.05):
     rng = np.random.default_rng(seed)
     moduli = P.prime_pairs(4) if pair else P.primes(3)
     np_ = len(moduli)
     va = rng.integers(-4, 5, size=1 << len(la)).astype(np.int32)
-    va[rng.random(va.size) < 0.05] = oracle.NEG
+    va[rng.random(va.size) < neg] = oracle.NEG
     vb = rng.integers(-4, 5, size=1 << len(lb)).astype(np.int32)
-    vb[rng.random(vb.size) < 0.05] = oracle.NEG
+    vb[rng.random(vb.size) < neg] = oracle.NEG
 
     def planes(v, unit):
         if unit:
@@ -724,3 +724,30 @@ def test_contract_outer_counting(P, case, form, shift):
 def test_contract_outer_unit_counts(P, case, unit):
     la, lb, lc = OUTER[case]
     _outer_run(P, la, lb, lc, True, 2100 + case, unitA=unit[0], unitB=unit[1])
+
+
+# The general streaming counting path with the same count-word layouts: summed
+# labels on A's top bits, so a thread's four outputs are A's and C's two lowest bits
+# (128-bit value and count-word loads of A, 128-bit count stores) when the count
+# tensors start on 16 bytes, and one word at a time when they are offset by a word.
+VEC_COUNT = [
+    (list(range(15)), [14], list(range(14))),                 # one summed label, B a vertex-like tensor
+    (list(range(16)), [14, 15], list(range(14))),             # two summed labels from B
+    (list(range(15)), [14, 30], list(range(14)) + [30]),      # summed label plus a B-only label on top
+]
+
+
+@pytest.mark.parametrize("case", range(len(VEC_COUNT)))
+@pytest.mark.parametrize("form", ["pair", "wide"])
+@pytest.mark.parametrize("shift", [(0, 0), (1, 0), (0, 1)])
+def test_contract_count_word_layouts(P, case, form, shift):
+    la, lb, lc = VEC_COUNT[case]
+    _outer_run(P, la, lb, lc, form == "pair", 2200 + case, sa=shift[0], sc=shift[1])
+
+
+@pytest.mark.parametrize("case", range(len(VEC_COUNT)))
+@pytest.mark.parametrize("unit", [(True, False), (False, True)])
+def test_contract_count_word_layouts_unit(P, case, unit):
+    la, lb, lc = VEC_COUNT[case]
+    _outer_run(P, la, lb, lc, True, 2300 + case, unitA=unit[0], unitB=unit[1])
+
