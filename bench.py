@@ -87,29 +87,6 @@ def max_over_ranks(values, dist, device):
     return [float(x) for x in t]
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "launch_list_ksg30x30_bbtn.md")
-TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, instance 0 of this workload "
-                  "(profiles/launch_list_ksg30x30_bbtn.md)")
-
-
-def ncu_traffic():
-    """DRAM bytes per launch of each kernel from the committed ncu summary of the
-    30x30 workload (its table rows read '| `kernel` (...) | launches | ... | N MB |').
-    Kernels whose row is marked 'stale' (changed since the capture) are left out."""
-    out = {}
-    try:
-        import re
-        for line in open(TRAFFIC_FILE):
-            if "stale" in line:
-                continue
-            m = re.match(r"\|\s*`([^`]+)`.*\|\s*([\d.]+)\s*MB\s*\|\s*$", line)
-            if m:
-                out[m.group(1)] = float(m.group(2)) * 1e6
-    except OSError:
-        pass
-    return out
-
-
 RATIO_FILE = os.path.join(ROOT, "profiles", "dram_traffic_kernel_cases.md")
 
 
@@ -433,14 +410,16 @@ def run_ours(args, rank, world, local_rank, wl):
         prof.close()
     peak, peak_kind = measured_peaks()
     alu, alu_src = alu_peak()
-    traffic = ncu_traffic() if not spin else {}
     ratios = ncu_ratios()
 
     def entry(kernel, ncu_name, bound, ms, work, launches, pk, unit, source, scale, bytes_=None):
         ach = work / (ms * scale) if ms else 0.0
         per_launch = (bytes_ / max(launches, 1)) if bytes_ else None
-        tr, tsrc = traffic.get(ncu_name), TRAFFIC_SOURCE if ncu_name in traffic else None
-        if tr is None and per_launch and ncu_name in ratios:
+        # traffic per launch: the kernel's measured DRAM bytes over algorithmic bytes
+        # on its bench case, times this workload's algorithmic bytes per launch (the
+        # same launches the achieved figure averages)
+        tr, tsrc = None, None
+        if per_launch and ncu_name in ratios:
             tr = ratios[ncu_name] * per_launch
             tsrc = (f"ncu DRAM bytes / algorithmic bytes = {ratios[ncu_name]:.3f} on this kernel's bench case "
                     "(profiles/dram_traffic_kernel_cases.md), times this workload's algorithmic bytes per launch")

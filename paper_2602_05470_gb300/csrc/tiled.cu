@@ -470,10 +470,11 @@ struct TArgs {
     Groups g[NB];
 };
 
-// two blocks per SM except for 64 x 64 counting tiles (their 4 x 4 outputs x NP
-// residue accumulators take the whole register file of one block)
+// three blocks per SM for values only (78 registers), two for 64 x 16 counting tiles,
+// one for 64 x 64 counting tiles (their 4 x 4 outputs x NP residue accumulators take
+// the whole register file of one block)
 template <int NP, int NB, bool V16, int TNC, bool PR>
-__global__ void __launch_bounds__(kThr, (NP == 0 || TNC == 16) ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
+__global__ void __launch_bounds__(kThr, NP == 0 ? 3 : TNC == 16 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
         tiled_body<NP, V16, TNC, PR>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);

@@ -751,3 +751,125 @@ def test_contract_count_word_layouts_unit(P, case, unit):
     la, lb, lc = VEC_COUNT[case]
     _outer_run(P, la, lb, lc, True, 2300 + case, unitA=unit[0], unitB=unit[1])
 
+
+# Counting steps with long sums (64 to 256 summed assignments per output) whose
+# shapes neither the register-tiled nor the split-K kernel takes (2^16 outputs, no
+# or one B-only label): the streaming kernel's two passes, with many ties.
+ONLINE = [
+    (list(range(22)), list(range(16, 22)), list(range(16))),                       # 6 summed labels on A's top bits
+    (list(range(100, 106)) + list(range(16)), list(range(100, 106)), list(range(16))),  # summed at A's low bits
+    (list(range(21)), list(range(15, 21)) + [40], list(range(15)) + [40]),         # plus a B-only output label
+    (list(range(24)), list(range(16, 24)), list(range(16))),                       # 8 summed labels
+]
+
+
+@pytest.mark.parametrize("case", range(len(ONLINE)))
+@pytest.mark.parametrize("form", ["pair", "wide"])
+def test_contract_one_pass_long_sums(P, case, form):
+    la, lb, lc = ONLINE[case]
+    _outer_run(P, la, lb, lc, form == "pair", 2400 + case, sc=case % 2)
+
+
+@pytest.mark.parametrize("case", [0, 2])
+@pytest.mark.parametrize("unit", [(True, False), (False, True)])
+def test_contract_one_pass_unit_counts(P, case, unit):
+    la, lb, lc = ONLINE[case]
+    _outer_run(P, la, lb, lc, True, 2500 + case, unitA=unit[0], unitB=unit[1])
+
+
+def test_contract_one_pass_infeasible_outputs(P):
+    """Mostly infeasible operands: many outputs have no feasible assignment and keep
+    their largest infeasible sum with count 0, as the oracle's definition stores them."""
+    la, lb, lc = ONLINE[0]
+    _outer_run(P, la, lb, lc, True, 2600, neg=0.95)
+
+
+# Big-by-big steps whose sum is shorter than the tiled kernel's 16-deep chunk (4 or 8
+# summed assignments): the streaming kernel gathers both operands.
+TILED_SHORT = [
+    # (m, n, k, batch, A's first group, B's first group, C order)
+    (6, 6, 2, 1, "m", "k", "mnb"),   # 4 summed: three quarters of the chunk padded
+    (6, 6, 3, 2, "k", "n", "nmb"),   # 8 summed
+    (7, 4, 3, 1, "k", "k", "bnm"),   # 8 summed, 64 x 16 tiles
+    (6, 5, 2, 0, "m", "n", "mn"),    # 4 summed, 5 B-only labels
+]
+
+
+@pytest.mark.parametrize("case", range(len(TILED_SHORT)))
+@pytest.mark.parametrize("np_", [0, 1, 3])
+def test_contract_tiled_short_sums(P, case, np_):
+    la, lb, lc = _tiled_case(*TILED_SHORT[case])
+    rng = np.random.default_rng(2700 + case)
+    primes = P.primes(np_)
+    A = _rand(rng, len(la), max(np_, 1), -4, 4, neg_frac=0.05)
+    B = _rand(rng, len(lb), max(np_, 1), -4, 4, neg_frac=0.05)
+    A = (A[0], A[1][:np_])
+    B = (B[0], B[1][:np_])
+    vc, cc = _run(P, la, A, lb, B, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, primes)
+    assert np.array_equal(vc, ov)
+    assert np.array_equal(cc, oc)
+
+
+@pytest.mark.parametrize("case", range(len(TILED_SHORT)))
+def test_contract_tiled_short_sums_pair(P, case):
+    la, lb, lc = _tiled_case(*TILED_SHORT[case])
+    _pair_case(P, la, lb, lc, 4, 2800 + case, lo=-4, hi=4)
+
+
+@pytest.mark.parametrize("case", range(len(TILED_SHORT)))
+def test_contract_tiled_short_sums_values16(P, case):
+    la, lb, lc = _tiled_case(*TILED_SHORT[case])
+    rng = np.random.default_rng(2900 + case)
+    va = rng.integers(-2000, 2000, size=1 << len(la)).astype(np.int32)
+    vb = rng.integers(-2000, 2000, size=1 << len(lb)).astype(np.int32)
+    va[rng.random(va.size) < 0.8] = oracle.NEG
+    vb[rng.random(vb.size) < 0.8] = oracle.NEG
+    vc = P.contract_values16(la, torch.from_numpy(va).cuda(), lb, torch.from_numpy(vb).cuda(), lc)
+    torch.cuda.synchronize()
+    got = vc.cpu().numpy()
+    ov, _ = oracle.contract(la, va, np.zeros((0, va.size), np.uint64), lb, vb, np.zeros((0, vb.size), np.uint64),
+                            lc, [])
+    feas = ov >= -(1 << 28)
+    assert feas.any() and (~feas).any()
+    assert np.array_equal(got[feas], ov[feas])
+    assert (got[~feas] < -(1 << 28)).all()
+
+
+# Steps with 2^16..2^18 outputs and long sums that the register-tiled kernel does not
+# take (the streaming kernel then runs only 2^14..2^16 threads through the sums).
+FEW_GROUPS = [
+    (list(range(16)) + list(range(100, 106)), list(range(100, 106)) + [30], list(range(16)) + [30]),  # rc 17, rs 6
+    (list(range(100, 108)) + list(range(16)), list(range(100, 108)), list(range(16))),  # summed at A's low bits
+    (list(range(18)) + list(range(100, 106)), list(range(100, 106)) + [17], list(range(18))),  # rc 18, a batch label
+]
+
+
+@pytest.mark.parametrize("case", range(len(FEW_GROUPS)))
+@pytest.mark.parametrize("form", ["pair", "wide"])
+def test_contract_few_groups_long_sums(P, case, form):
+    la, lb, lc = FEW_GROUPS[case]
+    _outer_run(P, la, lb, lc, form == "pair", 3000 + case, sc=case % 2)
+
+
+@pytest.mark.parametrize("case", range(len(FEW_GROUPS)))
+def test_contract_few_groups_long_sums_values(P, case):
+    la, lb, lc = FEW_GROUPS[case]
+    rng = np.random.default_rng(3100 + case)
+    A = _rand(rng, len(la), 1, -4, 4, neg_frac=0.05)
+    B = _rand(rng, len(lb), 1, -4, 4, neg_frac=0.05)
+    A, B = (A[0], A[1][:0]), (B[0], B[1][:0])
+    vc, _ = _run(P, la, A, lb, B, lc, [])
+    ov, _ = oracle.contract(la, A[0], A[1], lb, B[0], B[1], lc, [])
+    assert np.array_equal(vc, ov)
+
+
+def test_contract_few_groups_long_sums_reduction(P):
+    """A single-operand reduction with 2^16 outputs of 64 terms each."""
+    la, lc = list(range(22)), list(range(16))
+    rng = np.random.default_rng(3200)
+    primes = P.primes(3)
+    A = _rand(rng, len(la), 3, -4, 4, neg_frac=0.05)
+    vc, cc = _run(P, la, A, None, None, lc, primes)
+    ov, oc = oracle.contract(la, A[0], A[1], None, None, None, lc, primes)
+    assert np.array_equal(vc, ov) and np.array_equal(cc, oc)
