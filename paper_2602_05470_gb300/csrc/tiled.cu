@@ -389,6 +389,13 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                     }
                     if (cm[i][j] == best[i][j] && cm[i][j] >= kFiniteMin) {
                         const int mi = crow(ty, i), nj = ccol(tx, j);
+                        // the chunk's maximising k as a bit mask: its 32 shared-memory
+                        // loads are independent, where a compare-and-branch per k made
+                        // each wait for the last; then only the set bits are visited
+                        uint32_t tie = 0;
+#pragma unroll 8
+                        for (int kk = 0; kk < TK; kk++)
+                            tie |= (uint32_t)(cvA[kk][mi] + cvB[kk][nj] == cm[i][j]) << kk;
                         if constexpr (PR) {
                             // Two residues per word, each accumulated below 2q < 2^31 (not
                             // canonical until the store). A chunk's sum starts from the
@@ -401,8 +408,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                                 s0[t] = (uint32_t)acc[i][j][t];
                                 s1[t] = acc[i][j][t] >> 32;
                             }
-                            for (int kk = 0; kk < TK; kk++) {
-                                if (cvA[kk][mi] + cvB[kk][nj] != cm[i][j]) continue;
+                            for (uint32_t m = tie; m; m &= m - 1) {
+                                const int kk = __ffs(m) - 1;
 #pragma unroll
                                 for (int t = 0; t < NP; t++) {
                                     const uint64_t x = ua ? one : ccA[t][kk][mi], y = ub ? one : ccB[t][kk][nj];
@@ -419,8 +426,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                             u128 part[NP];
 #pragma unroll
                             for (int t = 0; t < NP; t++) part[t] = 0;
-                            for (int kk = 0; kk < TK; kk++) {
-                                if (cvA[kk][mi] + cvB[kk][nj] != cm[i][j]) continue;
+                            for (uint32_t m = tie; m; m &= m - 1) {
+                                const int kk = __ffs(m) - 1;
 #pragma unroll
                                 for (int t = 0; t < NP; t++) {
                                     const uint64_t x = ua ? one : ccA[t][kk][mi], y = ub ? one : ccB[t][kk][nj];
@@ -502,8 +509,9 @@ size_t tiled_smem(int np, int tn) {
 }
 
 // column tile of a step: 64 when its B-only group has at least 6 labels, else 16
-// (64 x 16 also for every counting step was measured: faster on random values, 15%
-// slower on the workload's counting steps)
+// (64 x 16 for every counting step was measured too: faster on random values; on the
+// workload's counting steps 15% slower with the full per-block tables, 4% faster with
+// the trimmed ones, before the spread layout made the 64 x 64 tiles 20% faster)
 inline int column_tile(const Groups &g) { return g.nn >= 6 ? 64 : 16; }
 
 template <int NP, int NB, bool V16, int TNC, bool PR>
