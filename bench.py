@@ -452,7 +452,7 @@ def run_ours(args, rank, world, local_rank, wl):
         entry("k_contract4 value-only (streaming gather, K1v)", "k_contract4<0, 1, 16, 0>", "hbm",
               pb["prof_stream_ms"], pb["prof_stream_bytes"], pb["prof_stream_launches"], peak, "GB/s",
               peak_kind + " HBM copy", 1e6, pb["prof_stream_bytes"]),
-        entry(f"k_contract4 counting (streaming gather, K1v, {planes} count planes of {cform})",
+        entry(f"k_contract4 + k_outer4 counting (streaming gather K1v and its one-term form, {planes} count planes of {cform})",
               "k_contract4<4, 1, 1, 1>", "hbm", pb["prof_scount_ms"], pb["prof_scount_bytes"],
               pb["prof_scount_launches"], peak, "GB/s", peak_kind + " HBM copy", 1e6, pb["prof_scount_bytes"]),
         tiled_entry("k_tiled value-only (register-tiled, K1t" + (", two 16-bit lanes per instruction)" if all16 else ")"),
