@@ -267,8 +267,8 @@ struct S4Args {
 };
 
 // Register caps: eight blocks per SM for values only (32 registers: every warp slot
-// filled, the kernel waits on HBM latency), three with up to
-// four count planes, fewer for the wide form's many planes (no spills in any).
+// filled, since the kernel waits on HBM latency), three with up to four count
+// planes, fewer for the wide form's many planes (no spills in any).
 template <int NP, bool HASB, int NB, bool PR>
 __global__ void __launch_bounds__(kThr, NP == 0 ? 8 : NP <= 4 ? 3 : NP <= 6 ? 2 : 1) k_contract4(const __grid_constant__ S4Args<NB> args) {
     __shared__ uint32_t tA[4][256];
