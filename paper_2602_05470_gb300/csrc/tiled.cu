@@ -7,12 +7,13 @@
 // b, m, n, k are groups of binary labels (batch / A-only / B-only / summed); every
 // group is gathered through bit-deposit tables, so no permutation pass runs in front
 // of the step. A block computes a 64 x 64 output tile of one batch entry (64 x 16
-// when the B-only group has only 4 or 5 labels, 4 x 1 per thread), 256
-// threads with a 4 x 4 micro-tile each, streaming K through shared memory in
-// chunks of 16 (int32 add + max, no tensor cores: max-plus is not an MMA). Values
-// only: the next chunk is prefetched into registers while the current one is
-// computed. With counts: one pass in which each chunk's maximum either restarts an
-// output's count or adds the products of the chunk's maximising k.
+// when the B-only group has only 4 or 5 labels, 4 x 1 per thread), 256 threads
+// with a 4 x 4 micro-tile each (512 threads with 4 x 2 for 64 x 64 counting tiles),
+// streaming K through shared memory in chunks of 16 (int32 add + max, no tensor
+// cores: max-plus is not an MMA). Values only: the next chunk is prefetched into
+// registers while the current one is computed. With counts: one pass in which each
+// chunk's maximum either restarts an output's count or adds the products of the
+// chunk's maximising k.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,6 +27,11 @@ namespace {
 
 constexpr int TM = 64, TK = 16;   // row tile, summed chunk
 constexpr int kThr = 256;
+// 64 x 64 counting tiles run 512 threads (4 x 2 outputs each): their accumulators
+// hold one 256-thread block per SM at 255 registers, where 512 threads at 128
+// registers give each SM twice the warps to hide the tie arithmetic's latency
+template <int NP, int TN>
+__host__ __device__ constexpr int tiled_threads() { return NP > 0 && TN == 64 ? 512 : kThr; }
 // Counting tiles: a thread's four rows / columns spread over the tile (r + 16 i)
 // instead of adjacent (4 r + i). Spread columns read the count tile without bank
 // conflicts and store the results coalesced; spread rows give every warp a share
@@ -56,8 +62,9 @@ __device__ __forceinline__ uint64_t deposit(uint64_t x, const int8_t *pos, int n
     return r;
 }
 
-// Per-thread part of a tile load: the thread fetches elements e = tid + r * 256
-// (r < 4) of every TM x TK chunk, with lanes along the operand's contiguous group.
+// Per-thread part of a tile load: the thread fetches elements e = tid + r * THR
+// (r < TM * TK / THR) of every TM x TK chunk, with lanes along the operand's
+// contiguous group.
 // Row / column offsets and the in-chunk k offsets do not change from chunk to
 // chunk, so they are summed once; a chunk only adds the deposit of its first k.
 template <int R>
@@ -66,11 +73,11 @@ struct Lanes {
     uint32_t sidx[R];   // shared-memory index ki * (ROWS + 4) + mi
 };
 
-template <int ROWS, int R>
+template <int ROWS, int R, int THR>
 __device__ __forceinline__ void lanes_setup(const uint32_t *rowoff, const uint32_t *koff, int fast_k, Lanes<R> &L) {
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        const int e = threadIdx.x + r * kThr;
+        const int e = threadIdx.x + r * THR;
         const int mi = fast_k ? (e >> 4) : (e & (ROWS - 1));
         const int ki = fast_k ? (e & (TK - 1)) : (e / ROWS);
         L.off[r] = rowoff[mi] + koff[ki];       // ki < 16: first byte table only
@@ -119,8 +126,11 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     // TN = 64: 4 x 4 outputs per thread; TN = 16: 4 x 1.
     static_assert(TN == 64 || TN == 16, "column tile");
     static_assert(!V16 || TN == 64, "16-bit lanes pair columns");
-    constexpr int MC = TN / 16;              // columns per thread
-    constexpr int RB = TN * TK / kThr;       // B elements a thread loads per chunk
+    constexpr int THR = tiled_threads<NP, TN>();
+    constexpr int MC = TN * 16 / THR;        // columns per thread (16 rows of threads)
+    constexpr int RA = TM * TK / THR;        // A elements a thread loads per chunk
+    constexpr int RB = TN * TK / THR;        // B elements a thread loads per chunk
+    static_assert(THR == kThr || (NP > 0 && kCountWarpRows && kColSpread), "512-thread tiles: counting layout");
     constexpr int TNB = TN == 64 ? 6 : 4;    // column bits of a tile
     const int K = 1 << G.nk;
     uint32_t *koffA = (uint32_t *)smem_raw;
@@ -143,7 +153,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     // Summed-label tables: table c holds the deposits of k bits 8c..8c+7, and only
     // its first 2^(bits of k in that byte) entries are ever read (a step with a
     // 16-long sum needs 16 of the 768), so only those are built.
-    for (int i = threadIdx.x; i < 768; i += kThr) {
+    for (int i = threadIdx.x; i < 768; i += THR) {
         const int c = i >> 8, v = i & 255;
         const int nbits = min(8, max(0, G.nk - 8 * c));
         if (v >> nbits) continue;
@@ -161,7 +171,8 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
     // four 64-thread groups) instead of four in the first 64 threads
     {
         const int which = threadIdx.x >> 6, i = threadIdx.x & 63;
-        if (which < 2) {
+        if (which >= 4) {
+        } else if (which < 2) {
             const uint64_t m = (uint64_t)tm * TM + i;
             (which ? rowC : rowA)[i] = (uint32_t)deposit(m, which ? G.mC : G.mA, G.nm);
         } else if (i < TN) {
@@ -169,13 +180,13 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
             (which == 3 ? colC : colB)[i] = (uint32_t)deposit(n, which == 3 ? G.nC : G.nB, G.nn);
         }
     }
-    static_assert(kThr == 256 && TM == 64, "four 64-thread table groups");
+    static_assert(THR >= 256 && TM == 64, "four 64-thread table groups");
     __syncthreads();
 
-    Lanes<4> LA;
+    Lanes<RA> LA;
     Lanes<RB> LB;
-    lanes_setup<TM, 4>(rowA, koffA, fastA_k, LA);
-    lanes_setup<TN, RB>(colB, koffB, fastB_k, LB);
+    lanes_setup<TM, RA, THR>(rowA, koffA, fastA_k, LA);
+    lanes_setup<TN, RB, THR>(colB, koffB, fastB_k, LB);
     const int32_t *__restrict__ Av = P.A.val + baseA;
     const int32_t *__restrict__ Bv = P.B.val + baseB;
     const uint64_t *__restrict__ Ac = P.A.cnt ? P.A.cnt + baseA : nullptr;
@@ -196,11 +207,11 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         uint32_t best2[4][2];
 #pragma unroll
         for (int i = 0; i < 4; i++) best2[i][0] = best2[i][1] = dup16(kNeg16);
-        int32_t ra[4], rb[RB];
+        int32_t ra[RA], rb[RB];
         auto gload = [&](int k0) {
             const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
-            for (int r = 0; r < 4; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
+            for (int r = 0; r < RA; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
 #pragma unroll
             for (int r = 0; r < RB; r++) rb[r] = __ldg(Bv + LB.off[r] + kb);
         };
@@ -208,7 +219,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         uint16_t *sB16f = &sB16[0][0];
         auto sstore = [&]() {
 #pragma unroll
-            for (int r = 0; r < 4; r++) sAf[LA.sidx[r]] = (int32_t)dup16(to16(ra[r]));
+            for (int r = 0; r < RA; r++) sAf[LA.sidx[r]] = (int32_t)dup16(to16(ra[r]));
 #pragma unroll
             for (int r = 0; r < RB; r++)   // same (k, n) position in the int16 tile, rows TN + 8 wide
                 sB16f[(LB.sidx[r] / (TN + 4)) * (TN + 8) + LB.sidx[r] % (TN + 4)] = (uint16_t)to16(rb[r]);
@@ -242,18 +253,18 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         // values only: int32 add + max. The next chunk's tiles are fetched into
         // registers while the current chunk is computed from shared memory.
         {
-            int32_t ra[4], rb[RB];
+            int32_t ra[RA], rb[RB];
             auto gload = [&](int k0) {
                 const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
-                for (int r = 0; r < 4; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
+                for (int r = 0; r < RA; r++) ra[r] = __ldg(Av + LA.off[r] + ka);
 #pragma unroll
                 for (int r = 0; r < RB; r++) rb[r] = __ldg(Bv + LB.off[r] + kb);
             };
             int32_t *sAf = &sA[0][0], *sBf = &sB[0][0];
             auto sstore = [&]() {
 #pragma unroll
-                for (int r = 0; r < 4; r++) sAf[LA.sidx[r]] = ra[r];
+                for (int r = 0; r < RA; r++) sAf[LA.sidx[r]] = ra[r];
 #pragma unroll
                 for (int r = 0; r < RB; r++) sBf[LB.sidx[r]] = rb[r];
             };
@@ -297,7 +308,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
         const int ty = kCountWarpRows ? (int)(threadIdx.x & 15) : (int)(threadIdx.x >> 4);
         // tile row / column of a thread's output (i, j)
         auto crow = [](int ty_, int i) { return kRowSpread ? ty_ + 16 * i : ty_ * 4 + i; };
-        auto ccol = [](int tx_, int j) { return MC == 4 && kColSpread ? tx_ + 16 * j : tx_ * MC + j; };
+        auto ccol = [](int tx_, int j) { return MC > 1 && kColSpread ? tx_ + (TN / MC) * j : tx_ * MC + j; };
         unsigned char *stage0 = (unsigned char *)(((uintptr_t)(colC + TN) + 15) & ~(uintptr_t)15);
         const bool ua = P.A.unit_counts, ub = P.B.unit_counts;
         const uint64_t one = PR ? 0x100000001ull : 1ull;
@@ -307,7 +318,7 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
             uint64_t *sc_a = (uint64_t *)(base + St::kVA + St::kVB), *sc_b = (uint64_t *)(base + St::kVA + St::kVB + St::kCA);
             const uint32_t ka = chunk_off(koffA, k0), kb = chunk_off(koffB, k0);
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
+            for (int r = 0; r < RA; r++) {
                 const uint32_t off = LA.off[r] + ka, si = LA.sidx[r];
                 cp_async4(sv_a + si, Av + off);
                 if (!ua) {
@@ -364,9 +375,9 @@ __device__ __forceinline__ void tiled_body(const ContractParams &P, const Groups
                     const int4 a4 = *(const int4 *)&cvA[kk][ty * 4];
                     a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
                 }
-                if constexpr (MC == 4 && kColSpread) {
+                if constexpr (MC > 1 && kColSpread) {
 #pragma unroll
-                    for (int j = 0; j < 4; j++) bb[j] = cvB[kk][tx + 16 * j];
+                    for (int j = 0; j < MC; j++) bb[j] = cvB[kk][tx + (TN / MC) * j];
                 } else if constexpr (MC == 4) {
                     const int4 b4 = *(const int4 *)&cvB[kk][tx * 4];
                     bb[0] = b4.x; bb[1] = b4.y; bb[2] = b4.z; bb[3] = b4.w;
@@ -481,7 +492,7 @@ struct TArgs {
 // one for 64 x 64 counting tiles (their 4 x 4 outputs x NP residue accumulators take
 // the whole register file of one block)
 template <int NP, int NB, bool V16, int TNC, bool PR>
-__global__ void __launch_bounds__(kThr, NP == 0 ? 3 : TNC == 16 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
+__global__ void __launch_bounds__(tiled_threads<NP, TNC>(), NP == 0 ? 3 : TNC == 16 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
         tiled_body<NP, V16, TNC, PR>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
@@ -536,7 +547,7 @@ cudaError_t launch_t(const ContractParams *ps, const Groups *gs, const int *fa, 
         cudaError_t e = allow_max_dynamic_smem<k_tiled<NP, NB, V16, TNC, PR>>();
         if (e != cudaSuccess) return e;
     }
-    k_tiled<NP, NB, V16, TNC, PR><<<(unsigned)total, kThr, smem, s>>>(a);
+    k_tiled<NP, NB, V16, TNC, PR><<<(unsigned)total, tiled_threads<NP, TNC>(), smem, s>>>(a);
     return cudaGetLastError();
 }
 
