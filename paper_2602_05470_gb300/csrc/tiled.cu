@@ -488,11 +488,11 @@ struct TArgs {
     Groups g[NB];
 };
 
-// three blocks per SM for values only (78 registers), two for 64 x 16 counting tiles,
-// one for 64 x 64 counting tiles (their 4 x 4 outputs x NP residue accumulators take
-// the whole register file of one block)
+// four blocks per SM for values only (64 registers, no spills), two for 64 x 16
+// counting tiles, one 512-thread block for 64 x 64 counting tiles (their 4 x 2
+// outputs x NP residue accumulators take 128 registers)
 template <int NP, int NB, bool V16, int TNC, bool PR>
-__global__ void __launch_bounds__(tiled_threads<NP, TNC>(), NP == 0 ? 3 : TNC == 16 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
+__global__ void __launch_bounds__(tiled_threads<NP, TNC>(), NP == 0 ? 4 : TNC == 16 ? 2 : 1) k_tiled(const __grid_constant__ TArgs<NB> args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if constexpr (NB == 1) {
         tiled_body<NP, V16, TNC, PR>(args.p[0], args.g[0], args.fa[0], args.fb[0], blockIdx.x, smem_raw);
