@@ -255,7 +255,11 @@ typedef struct {
     int count_check;         /* overflow guard: -1 auto, 0 off, 1 on (default -1) */
     int use_symmetry;        /* spin-flip symmetry when every field is 0 (default 1) */
     int verbose;             /* progress to stderr (default 0) */
-    int profile;             /* time every contraction launch with CUDA events (default 0) */
+    int profile;             /* time every contraction launch with CUDA events (default 0);
+                                with the environment variable BBTN_PROFILE_DUMP set to a
+                                path, a profiled solve also writes one CSV row per launch
+                                there (operand and output ranks, summed labels, algorithmic
+                                bytes and ops, milliseconds, kernel kind, leaves batched) */
     int max_slices_log2;     /* sliced mode: refuse more than 2^this slices (default 30) */
     int branch_lookahead;    /* seed of each branching region: the variable, among the this-many
                                 carrying the most overflow, whose branching has the smallest
