@@ -287,6 +287,11 @@ typedef struct {
     int no_chain_fusion;     /* 1: run every value-only step as its own launch instead of fusing
                                 chains of steps in which a big tensor absorbs small network tensors
                                 into one pass (default 0: fused; the results are identical) */
+    int order_restarts;      /* root contraction order: this many annealed restarts (host
+                                threads), every odd one started from a min-fill elimination order
+                                with its own tie-breaking seed, 0..64 (default 0: four restarts,
+                                one of them from min-fill). The results are identical; only the
+                                tree, and so the work and the branching, change */
 } bbtn_opts;
 
 typedef struct {

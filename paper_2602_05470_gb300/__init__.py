@@ -195,8 +195,9 @@ class Solver:
     """Owns one library context (a CUDA stream + device arena). Keyword options
     mirror `bbtn_opts` in include/bbtn.h; among them `n_primes` count planes (two
     residues mod 30-bit primes per word, or one mod a 61-bit prime with
-    `wide_counts=True`) and `leaf_trials` (own contraction orders for counting
-    leaves, off by default). Contexts on different streams may solve concurrently
+    `wide_counts=True`), `leaf_trials` (own contraction orders for counting
+    leaves, off by default) and `order_restarts` (restarts of the root order search,
+    every odd one from a min-fill order; 0: the default four). Contexts on different streams may solve concurrently
     from different host threads."""
 
     def __init__(self, mode: int = MODE_BBTN, space_cap_log2: int = 24, n_primes: int = 3, seed: int = 1,
@@ -204,7 +205,7 @@ class Solver:
                  count_check: int = -1, use_symmetry: bool = True, max_slices_log2: int = 30,
                  profile: bool = False, branch_lookahead: int = 1, leaf_trials: int = 0, autotune: bool = False,
                  wide_counts: bool = False, slice_sample: int = 0, arena_budget_mb: int = 0,
-                 chain_fusion: bool = True, stream=None, workspace=None):
+                 chain_fusion: bool = True, order_restarts: int = 0, stream=None, workspace=None):
         lib = _lib.load()
         o = Opts()
         lib.bbtn_default_opts(C.byref(o))
@@ -215,6 +216,7 @@ class Solver:
         o.leaf_trials, o.autotune, o.wide_counts = leaf_trials, int(autotune), int(wide_counts)
         o.slice_sample, o.arena_budget_mb = int(slice_sample), int(arena_budget_mb)
         o.no_chain_fusion = int(not chain_fusion)
+        o.order_restarts = int(order_restarts)
         self._ctx = C.c_void_p()
         check(lib.bbtn_create(C.byref(o), C.byref(self._ctx)))
         if stream is not None:

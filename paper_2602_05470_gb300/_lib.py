@@ -31,7 +31,8 @@ class Opts(C.Structure):
                 ("batch", C.c_int), ("use_gnn", C.c_int), ("count_check", C.c_int),
                 ("use_symmetry", C.c_int), ("verbose", C.c_int), ("profile", C.c_int),
                 ("max_slices_log2", C.c_int), ("branch_lookahead", C.c_int), ("leaf_trials", C.c_int),
-                ("autotune", C.c_int), ("wide_counts", C.c_int), ("slice_sample", C.c_int), ("arena_budget_mb", C.c_int), ("no_chain_fusion", C.c_int)]
+                ("autotune", C.c_int), ("wide_counts", C.c_int), ("slice_sample", C.c_int), ("arena_budget_mb", C.c_int), ("no_chain_fusion", C.c_int),
+                ("order_restarts", C.c_int)]
 
 
 class Stats(C.Structure):

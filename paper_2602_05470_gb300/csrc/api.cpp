@@ -349,6 +349,7 @@ void bbtn_default_opts(bbtn_opts *o) {
     o->slice_sample = 0;
     o->arena_budget_mb = 0;
     o->no_chain_fusion = 0;
+    o->order_restarts = 0;
 }
 
 int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
@@ -366,6 +367,7 @@ int bbtn_create(const bbtn_opts *opts, bbtn_ctx **out) {
         if (o.sa_iters < 0) fail(BBTN_EINVAL, "sa_iters < 0");
         if (o.branch_lookahead < 0 || o.branch_lookahead > 1024) fail(BBTN_EINVAL, "branch_lookahead outside 0..1024");
         if (o.leaf_trials < 0 || o.leaf_trials > 256) fail(BBTN_EINVAL, "leaf_trials outside 0..256");
+        if (o.order_restarts < 0 || o.order_restarts > 64) fail(BBTN_EINVAL, "order_restarts outside 0..64");
         // without a usable device the context still plans on the host (bbtn_analyze);
         // every call that needs the device then fails with BBTN_ECUDA
         if (cudaGetDevice(&ctx->device) == cudaSuccess &&

@@ -462,15 +462,16 @@ void tree_sa(CTree &t, const SAParams &sp, uint64_t seed) {
 }
 
 CTree find_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, int cap, double w_rho,
-                 int trials, int sa_beta_steps, uint64_t seed) {
+                 int trials, int sa_beta_steps, uint64_t seed, bool minfill_odd) {
     // independent restarts, one host thread each; the best objective wins (ties:
     // the lowest trial index, so the result does not depend on thread timing)
     const int nt = std::max(1, trials);
     std::vector<CTree> trees(nt);
     std::vector<double> f(nt, std::numeric_limits<double>::infinity());
     auto run = [&](int tr) {
-        // restart 1 starts from a min-fill elimination order, the others from greedy
-        CTree t = tr == 1 ? elimination_order(leaf_labels, nvars, seed * 7919 + tr)
+        // restart 1 (every odd one with minfill_odd) starts from a min-fill elimination
+        // order, the others from greedy
+        CTree t = tr == 1 || (minfill_odd && tr % 2 == 1) ? elimination_order(leaf_labels, nvars, seed * 7919 + tr)
                           : greedy_order(leaf_labels, nvars, seed * 7919 + tr, tr == 0 ? 0.0 : 0.3);
         if (sa_beta_steps > 0) {
             SAParams sp;

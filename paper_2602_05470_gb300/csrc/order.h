@@ -58,9 +58,12 @@ struct SAParams {
 // log2(tc) + w_rho * rho.
 void tree_sa(CTree &t, const SAParams &sp, uint64_t seed);
 
-// Greedy + annealing with several restarts; returns the best tree.
+// Greedy + annealing with several restarts; returns the best tree. Restart 1 starts
+// from a min-fill elimination order, the others from greedy orders; with
+// minfill_odd every odd restart starts from a min-fill order (each with its own
+// tie-breaking seed).
 CTree find_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, int cap, double w_rho,
-                 int trials, int sa_beta_steps, uint64_t seed);
+                 int trials, int sa_beta_steps, uint64_t seed, bool minfill_odd = false);
 
 // Dynamic slicing: pick labels to fix (greedily, the one that lowers the
 // overflow most, then the one adding least time) until every tensor fits 2^cap.

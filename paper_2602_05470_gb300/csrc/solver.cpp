@@ -358,7 +358,7 @@ OrderCache &order_cache() {
 }
 
 uint64_t order_key(const std::vector<std::vector<int>> &labels, const std::vector<int8_t> &fx, int cap,
-                   double w_rho, int trials, int sa_iters, uint64_t seed) {
+                   double w_rho, int trials, int sa_iters, uint64_t seed, bool minfill_odd) {
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](uint64_t x) {
         h ^= x + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
@@ -376,6 +376,7 @@ uint64_t order_key(const std::vector<std::vector<int>> &labels, const std::vecto
     mix((uint64_t)trials);
     mix((uint64_t)sa_iters);
     mix(seed);
+    mix((uint64_t)minfill_odd);
     return h;
 }
 
@@ -389,26 +390,26 @@ void clear_order_cache() {
 
 // The root order: from the cache when this network (labels of its tensors and
 // the root's fixed variables) was ordered before with the same settings.
-CTree Solver::cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials) {
-    const uint64_t key = order_key(net_.labels, fx, cap, w_rho, trials, opts_.sa_iters, opts_.seed);
+CTree Solver::cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials, bool minfill_odd) {
+    const uint64_t key = order_key(net_.labels, fx, cap, w_rho, trials, opts_.sa_iters, opts_.seed, minfill_odd);
     OrderCache &c = order_cache();
     {
         std::lock_guard<std::mutex> lock(c.mu);
         auto it = c.trees.find(key);
         if (it != c.trees.end()) return it->second;
     }
-    CTree t = order_for(fx, cap, w_rho, trials);
+    CTree t = order_for(fx, cap, w_rho, trials, minfill_odd);
     std::lock_guard<std::mutex> lock(c.mu);
     if (c.trees.size() >= 256) c.trees.clear();
     c.trees[key] = t;
     return t;
 }
 
-CTree Solver::order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials) {
+CTree Solver::order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials, bool minfill_odd) {
     std::vector<std::vector<int>> ll(net_.labels.size());
     for (size_t i = 0; i < ll.size(); i++)
         for (int l : net_.labels[i]) if (fx[l] < 0) ll[i].push_back(l);
-    return find_order(ll, p_->n, cap, w_rho, trials, opts_.sa_iters, opts_.seed);
+    return find_order(ll, p_->n, cap, w_rho, trials, opts_.sa_iters, opts_.seed, minfill_odd);
 }
 
 // Exact reductions of a partial assignment (logical inference, paper: local
@@ -515,7 +516,10 @@ void Solver::setup_host(const Problem &p, bool want_count) {
     const double t0 = now_s();
     const int cap = opts_.space_cap_log2;
     const double w_rho = opts_.mode == BBTN_MODE_PLAIN ? 8.0 : 1.0;
-    tree_ = cached_order(fx0_, cap, w_rho, 4);
+    // root order: four restarts (one from min-fill), or opts.order_restarts with every
+    // odd one from min-fill
+    if (opts_.order_restarts > 0) tree_ = cached_order(fx0_, cap, w_rho, opts_.order_restarts, true);
+    else tree_ = cached_order(fx0_, cap, w_rho, 4);
     Cost c = tree_cost(tree_, cap);
     st_->tc_log2 = c.tc_log2;
     st_->sc_plain_log2 = c.sc;

@@ -113,8 +113,8 @@ class Solver {
     int64_t incumbent_heuristic();
     int64_t incumbent_learned();
     void simplify(std::vector<int8_t> &fx) const;
-    CTree order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
-    CTree cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials);
+    CTree order_for(const std::vector<int8_t> &fx, int cap, double w_rho, int trials, bool minfill_odd = false);
+    CTree cached_order(const std::vector<int8_t> &fx, int cap, double w_rho, int trials, bool minfill_odd = false);
 
     bbtn_opts opts_;
     cudaStream_t stream_;

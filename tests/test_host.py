@@ -317,3 +317,24 @@ def test_shard_counts_needs_shard_values(P):
     assert rc == P._lib.ESTATE
     assert b"shard_values" in lib.bbtn_last_error()
     s.close()
+
+
+def test_order_restarts_option(P):
+    """opts.order_restarts: 0..64 accepted, anything else rejected; with several
+    min-fill restarts the root orders of eight 30x30 workload instances take less
+    work in total than the default search's (host planning only)."""
+    for bad in (-1, 65):
+        with pytest.raises(P.BBTNError) as e:
+            P.Solver(order_restarts=bad)
+        assert e.value.code == P._lib.EINVAL
+    total = {}
+    for r in (0, 16):
+        ops = []
+        for idx in range(8):
+            inst = synth.kings_subgraph(30, 0.8, seed=synth.config_seed(2, idx))
+            s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, order_restarts=r)
+            P.clear_order_cache()
+            ops.append(s.analyze(inst)["ops"])
+            s.close()
+        total[r] = ops
+    assert sum(total[16]) < sum(total[0])
