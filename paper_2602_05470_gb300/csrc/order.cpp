@@ -247,30 +247,43 @@ CTree greedy_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, 
 // random key. Its widths on grid-like graphs are close to the sweep widths.
 static std::vector<int> min_fill_order(const std::vector<std::vector<int>> &leaf_labels, int nvars, uint64_t seed) {
     Rng rng(seed);
-    std::vector<std::vector<int>> adj(nvars);
+    // the interaction graph as one bit row per variable: a variable's degree is a
+    // popcount, its fill (non-adjacent pairs of neighbours) is C(d, 2) minus half the
+    // sum over neighbours u of |N(u) & N(v)|, and an elimination ORs the eliminated
+    // variable's row into its neighbours' rows
+    const int W = (nvars + 63) / 64;
+    std::vector<uint64_t> bits((size_t)nvars * W, 0);
+    auto row = [&](int v) { return bits.data() + (size_t)v * W; };
+    auto set_bit = [&](int v, int w) { row(v)[w >> 6] |= 1ull << (w & 63); };
     std::vector<char> used(nvars, 0);
     for (const auto &lab : leaf_labels)
         for (size_t i = 0; i < lab.size(); i++) {
             used[lab[i]] = 1;
             for (size_t j = i + 1; j < lab.size(); j++) {
-                adj[lab[i]].push_back(lab[j]);
-                adj[lab[j]].push_back(lab[i]);
+                set_bit(lab[i], lab[j]);
+                set_bit(lab[j], lab[i]);
             }
         }
-    for (auto &a : adj) {
-        std::sort(a.begin(), a.end());
-        a.erase(std::unique(a.begin(), a.end()), a.end());
-    }
-    std::vector<int> mark(nvars, -1);
+    auto degree = [&](int v) {
+        const uint64_t *r = row(v);
+        int d = 0;
+        for (int k = 0; k < W; k++) d += __builtin_popcountll(r[k]);
+        return d;
+    };
+    // calls f(u) for every set bit u of the row r, in ascending order
+    auto for_bits = [&](const uint64_t *r, auto &&f) {
+        for (int k = 0; k < W; k++)
+            for (uint64_t x = r[k]; x; x &= x - 1) f(k * 64 + __builtin_ctzll(x));
+    };
     auto fill_of = [&](int v) {
-        int64_t f = 0;
-        const auto &N = adj[v];
-        for (size_t i = 0; i < N.size(); i++) {
-            for (int w : adj[N[i]]) mark[w] = N[i];
-            for (size_t j = i + 1; j < N.size(); j++)
-                if (mark[N[j]] != N[i]) f++;
-        }
-        return f;
+        const uint64_t *rv = row(v);
+        int64_t d = 0, adjacent2 = 0;
+        for_bits(rv, [&](int u) {
+            d++;
+            const uint64_t *ru = row(u);
+            for (int k = 0; k < W; k++) adjacent2 += __builtin_popcountll(ru[k] & rv[k]);
+        });
+        return d * (d - 1) / 2 - adjacent2 / 2;
     };
     std::vector<double> tieb(nvars);
     for (int v = 0; v < nvars; v++) tieb[v] = rng.uniform();
@@ -286,38 +299,36 @@ static std::vector<int> min_fill_order(const std::vector<std::vector<int>> &leaf
     for (int v = 0; v < nvars; v++)
         if (used[v]) {
             cur[v] = fill_of(v);
-            pq.push({cur[v], (int)adj[v].size(), tieb[v], v});
+            pq.push({cur[v], degree(v), tieb[v], v});
         }
     std::vector<int> order;
-    std::vector<int> touched;
+    std::vector<uint64_t> nb(W), touched(W);
     while (!pq.empty()) {
         Key k = pq.top();
         pq.pop();
         const int v = k.v;
-        if (gone[v] || k.fill != cur[v] || k.deg != (int)adj[v].size()) continue;
+        if (gone[v] || k.fill != cur[v] || k.deg != degree(v)) continue;
         gone[v] = 1;
         order.push_back(v);
-        const std::vector<int> N = adj[v];
         // N becomes a clique; v leaves the graph
-        for (int a : N) {
-            auto &A = adj[a];
-            A.erase(std::lower_bound(A.begin(), A.end(), v));
-            for (int b : N)
-                if (b != a && !std::binary_search(A.begin(), A.end(), b)) A.insert(std::upper_bound(A.begin(), A.end(), b), b);
-        }
-        adj[v].clear();
-        touched.clear();
-        for (int a : N) {
-            touched.push_back(a);
-            for (int w : adj[a]) touched.push_back(w);
-        }
-        std::sort(touched.begin(), touched.end());
-        touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
-        for (int w : touched) {
-            if (gone[w]) continue;
+        std::copy(row(v), row(v) + W, nb.begin());
+        for_bits(nb.data(), [&](int a) {
+            uint64_t *ra = row(a);
+            for (int k2 = 0; k2 < W; k2++) ra[k2] |= nb[k2];
+            ra[a >> 6] &= ~(1ull << (a & 63));
+            ra[v >> 6] &= ~(1ull << (v & 63));
+        });
+        std::fill(row(v), row(v) + W, 0ull);
+        std::copy(nb.begin(), nb.end(), touched.begin());
+        for_bits(nb.data(), [&](int a) {
+            const uint64_t *ra = row(a);
+            for (int k2 = 0; k2 < W; k2++) touched[k2] |= ra[k2];
+        });
+        for_bits(touched.data(), [&](int w) {
+            if (gone[w]) return;
             cur[w] = fill_of(w);
-            pq.push({cur[w], (int)adj[w].size(), tieb[w], w});
-        }
+            pq.push({cur[w], degree(w), tieb[w], w});
+        });
     }
     return order;
 }
