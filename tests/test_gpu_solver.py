@@ -255,7 +255,7 @@ def test_concurrent_contexts_on_two_streams(P):
 
 def test_ksg_30x30_all_32_instances(P):
     """Every instance of the 30x30 King's-subgraph workload (filling 0.8, cap 2^24,
-    the benchmark's solver settings) against the stored oracle answers: MIS size,
+    the library's default order search) against the stored oracle answers: MIS size,
     exact degeneracy through the CRT, and an independent set of that size."""
     with open(GOLDEN) as f:
         rows = json.load(f)["ksg_30x30_f2"]
@@ -264,6 +264,20 @@ def test_ksg_30x30_all_32_instances(P):
     for row in rows:
         inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
         res = s.solve(inst, count=True, config=True)
+        _check(inst, res, row["alpha"], int(row["count"]))
+        assert res.stats["sc_log2"] <= 24
+
+
+def test_ksg_30x30_all_32_instances_sixteen_restarts(P):
+    """The same 32 instances with the benchmark's root order search (16 restarts, every
+    odd one from a min-fill order): other contraction trees and fewer leaves, the
+    same MIS sizes and exact degeneracies as the oracle."""
+    with open(GOLDEN) as f:
+        rows = json.load(f)["ksg_30x30_f2"]
+    s = P.Solver(mode=P.MODE_BBTN, space_cap_log2=24, n_primes=3, batch=64, order_restarts=16)
+    for row in rows:
+        inst = synth.kings_subgraph(30, 0.8, seed=row["seed"])
+        res = s.solve(inst, count=True)
         _check(inst, res, row["alpha"], int(row["count"]))
         assert res.stats["sc_log2"] <= 24
 
